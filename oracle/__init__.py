@@ -1,0 +1,141 @@
+"""CPU oracle for the upper hood (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its
+``cpu_baseline`` leg and its reference arm) may import this package. The
+product path never does: the CUDA library fails loudly instead of falling back
+here.
+
+``oracle.c`` holds the arithmetic (Andrew's monotone chain and an O(n^3) brute
+force, both with exact int64 orientation). This module only compiles it with
+gcc, loads it with ctypes and marshals numpy arrays.
+
+Parity status: every function here is pinned by ``tests/test_oracle.py``
+(brute force, closed forms, Qhull in general position, invariants, Python
+big-integer orientation).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i8p = ctypes.POINTER(ctypes.c_int8)
+            lib.oracle_upper_hull.restype = ctypes.c_int64
+            lib.oracle_upper_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_upper_hull_brute.restype = ctypes.c_int64
+            lib.oracle_upper_hull_brute.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_orient_sign.restype = ctypes.c_int
+            lib.oracle_orient_sign.argtypes = [ctypes.c_int32] * 6
+            lib.oracle_orient_signs.restype = None
+            lib.oracle_orient_signs.argtypes = [i32p, i32p, ctypes.c_int64, i8p]
+            lib.oracle_upper_hull_batched.restype = None
+            lib.oracle_upper_hull_batched.argtypes = [i32p, i32p, i64p, ctypes.c_int64, i32p, i32p]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _ints(kx, ky):
+    kx = np.ascontiguousarray(kx, dtype=np.int32)
+    ky = np.ascontiguousarray(ky, dtype=np.int32)
+    if kx.shape != ky.shape or kx.ndim != 1:
+        raise ValueError("kx and ky must be 1-D arrays of equal length")
+    return kx, ky
+
+
+def upper_hull(kx, ky) -> np.ndarray:
+    """Indices of the strict upper-hood corners, left to right (monotone chain)."""
+    kx, ky = _ints(kx, ky)
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    h = _load().oracle_upper_hull(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                  kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def upper_hull_brute(kx, ky) -> np.ndarray:
+    """Same set by the O(n^3) witness-pair definition (small n only)."""
+    kx, ky = _ints(kx, ky)
+    if kx.shape[0] > 2048:
+        raise ValueError("brute force is O(n^3); keep n small")
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    h = _load().oracle_upper_hull_brute(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                        kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def orient_sign(o, a, b) -> int:
+    """sign(det(a - o, b - o)) for integer grid points given as (kx, ky) pairs."""
+    return int(_load().oracle_orient_sign(int(o[0]), int(o[1]), int(a[0]), int(a[1]),
+                                          int(b[0]), int(b[1])))
+
+
+def orient_signs(kx, ky) -> np.ndarray:
+    """Signs for consecutive triples (3t, 3t+1, 3t+2) of the given points."""
+    kx, ky = _ints(kx, ky)
+    if kx.shape[0] % 3:
+        raise ValueError("need a multiple of 3 points")
+    out = np.empty(kx.shape[0] // 3, dtype=np.int8)
+    _load().oracle_orient_signs(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                out.shape[0], _p(out, ctypes.c_int8))
+    return out
+
+
+def upper_hull_batched(kx, ky, offsets):
+    """Per-set corners: returns (out, counts) with set s at out[offsets[s]:offsets[s]+counts[s]]."""
+    kx, ky = _ints(kx, ky)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    num_sets = offsets.shape[0] - 1
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    counts = np.empty(max(1, num_sets), dtype=np.int32)
+    _load().oracle_upper_hull_batched(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                      _p(offsets, ctypes.c_int64), num_sets,
+                                      _p(out, ctypes.c_int32), _p(counts, ctypes.c_int32))
+    return out, counts[:num_sets].copy()
+
+
+def bridge(p_kx, p_ky, q_kx, q_ky):
+    """Bridge (upper common tangent) of two hoods P and Q, P entirely lex-left of Q.
+
+    Defined from the merged hood (paper Section 2, match_and_merge outline):
+    H(P u Q) = P[0..p] ++ Q[q..], so p is the last corner of the merged hood
+    that comes from P and q the first that comes from Q. Returns (p, q), with
+    -1 for a side that contributes nothing.
+    """
+    kx = np.concatenate([np.asarray(p_kx, np.int32), np.asarray(q_kx, np.int32)])
+    ky = np.concatenate([np.asarray(p_ky, np.int32), np.asarray(q_ky, np.int32)])
+    hp = len(p_kx)
+    h = upper_hull(kx, ky)
+    from_p = h[h < hp]
+    from_q = h[h >= hp]
+    p = int(from_p[-1]) if from_p.size else -1
+    q = int(from_q[0]) - hp if from_q.size else -1
+    return p, q
