@@ -1,0 +1,223 @@
+/*
+ * wg.h -- C ABI of libwagener: the upper hood (upper convex hull) of sorted
+ * planar points on one GB300 GPU, by the merge schedule of Wagener's PRAM
+ * algorithm as implemented in C. O Dunlaing, "CUDA implementation of
+ * Wagener's 2D convex hull PRAM algorithm" (arXiv:1203.5004).
+ *
+ * The problem (paper Section 2): n points presented left to right; return the
+ * corners of their upper hood, left to right. Every stage of the paper's
+ * schedule merges adjacent pairs of hoods: it finds the bridge (upper common
+ * tangent) of each pair with the paper's g/f tests and LOW/EQUAL/HIGH votes
+ * (Section 2, match_and_merge, phases mam 1 to mam 5) and keeps
+ * P[0..p] ++ Q[q..] (mam 6).
+ *
+ * Input contract shared by every entry point
+ *   - points: float32 pairs (x, y), interleaved, 8-byte aligned; x and y are
+ *     integers times 2^-24 in [0, 1) (the "grid"); sorted lexicographically by
+ *     (x, y). Grid coordinates make every coordinate difference exact in
+ *     float32, which the orientation predicate relies on (see wg_options).
+ *     Off-grid or unsorted input gives unspecified (but memory-safe) output
+ *     unless validation is enabled.
+ *   - Readings fixed where the paper is silent: equal x values are allowed
+ *     (order is lexicographic); a point equal to an earlier point is never a
+ *     corner (first occurrence wins); collinear points are not corners (each
+ *     corner is a strict right turn); any n >= 0 is accepted.
+ *   - Output: the input indices of the corners, strictly increasing, and
+ *     their count. n = 0 gives count 0; otherwise index 0 is always first.
+ *
+ * Ownership and asynchrony
+ *   - The caller owns every buffer. The library never allocates device memory
+ *     inside a call. Device pointers must stay valid until the stream work
+ *     completes.
+ *   - Calls enqueue work on `stream` (NULL = legacy default stream) and return
+ *     without synchronising, unless stated otherwise. The return code covers
+ *     argument checks and launch errors. Errors found on the device (a bounded
+ *     wait that gave up, invalid input in validation mode) are recorded in a
+ *     status word inside the workspace; read it with wg_get_device_status.
+ *   - A workspace must be zero-filled once before its first use (cudaMemset);
+ *     every call leaves it ready for the next. Calls that share one workspace
+ *     must not overlap on the GPU (use one stream, or one workspace each).
+ */
+#ifndef WG_H_
+#define WG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *wg_stream_t; /* same type as cudaStream_t */
+
+typedef enum wg_status {
+    WG_OK = 0,
+    WG_ERR_INVALID_VALUE = 1, /* null pointer, negative size, misaligned pointer, bad option */
+    WG_ERR_WORKSPACE = 2,     /* workspace null or smaller than the size query returns */
+    WG_ERR_UNSORTED = 3,      /* validation: points not sorted by (x, y) */
+    WG_ERR_OFF_GRID = 4,      /* validation: a coordinate not k * 2^-24 in [0, 1) */
+    WG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up; output is not valid */
+    WG_ERR_CUDA = 6,          /* a CUDA runtime call failed (launch, copy, attribute) */
+    WG_ERR_UNSUPPORTED = 7    /* no usable sm_103 device, or a size beyond the limits */
+} wg_status;
+
+/* Orientation predicate precision (the only arithmetic on the path).
+ * WG_PRED_FILTERED: det(a - o, b - o) in float32 from exact differences;
+ *   the sign is accepted when |det| > 2^-22 (|t1| + |t2|), t1 and t2 being the
+ *   two rounded products, which bounds the rounding error; otherwise the
+ *   determinant is recomputed exactly in float64 (products of 24-bit
+ *   differences are exact there).
+ * WG_PRED_FP64: always the exact float64 evaluation. */
+typedef enum wg_pred_mode { WG_PRED_FILTERED = 0, WG_PRED_FP64 = 1 } wg_pred_mode;
+
+typedef struct wg_options {
+    int32_t pred_mode;       /* wg_pred_mode */
+    int32_t count_predicates;/* 1: count orientation tests and float64 fallbacks (slower) */
+    int32_t validate;        /* 1: check grid membership and order; report WG_ERR_* on device */
+    int32_t tile_config;     /* 0 = library choice (autotuned if wg_autotune ran); else 1..WG_NUM_TILE_CONFIGS */
+    int32_t segments_per_cta;/* 0 = library choice; else segments per resident CTA (1..8) */
+    int32_t reserved[3];
+} wg_options;
+
+#define WG_NUM_TILE_CONFIGS 3
+
+/* Fills *opts with the defaults (filtered predicate, no counters, no
+ * validation, library-chosen tiling). */
+void wg_options_default(wg_options *opts);
+
+/* ------------------------------------------------------------------------
+ * Single set, fused schedule (the fast path).
+ * Stages 1..log2(T) of the paper's schedule run inside one CTA per tile of T
+ * points (Section 2, stage loop of main, fused; Section 3, strips); each CTA
+ * merges its consecutive tile hoods into one segment hood; the last CTA to
+ * finish merges the segment hoods. One kernel launch.
+ *
+ * points    device, n (x, y) pairs as above
+ * n         0 <= n <= 2^31 - 1
+ * out_idx   device int32[max(n, 1)]: corners at out_idx[0..count). The
+ *           whole array is used as scratch during the call.
+ * out_count device int32[1]
+ * workspace device, >= wg_upper_hood_workspace_size(n) bytes, 256-B aligned
+ * Returns WG_OK or an argument/launch error.
+ * ---------------------------------------------------------------------- */
+size_t wg_upper_hood_workspace_size(int64_t n);
+wg_status wg_upper_hood(const float *points, int64_t n, int32_t *out_idx,
+                        int32_t *out_count, void *workspace, size_t ws_bytes,
+                        wg_stream_t stream);
+wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx,
+                           int32_t *out_count, void *workspace, size_t ws_bytes,
+                           const wg_options *opts, wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Single set, plain full-stage schedule: the paper's stage loop (Section 2,
+ * main) kept on the device, one kernel launch per stage d = 1, 2, 4, ... Each
+ * launch merges every adjacent pair of hoods (bridge by the sampled LOW/EQUAL/
+ * HIGH search, mam 1-5) and packs the merged hoods densely with a single-pass
+ * decoupled look-back scan (mam 6 with explicit lengths instead of REMOTE
+ * padding). Same output as wg_upper_hood; slower; kept as the unfused form.
+ * workspace >= wg_upper_hood_plain_workspace_size(n) bytes.
+ * ---------------------------------------------------------------------- */
+size_t wg_upper_hood_plain_workspace_size(int64_t n);
+wg_status wg_upper_hood_plain(const float *points, int64_t n, int32_t *out_idx,
+                              int32_t *out_count, void *workspace,
+                              size_t ws_bytes, const wg_options *opts,
+                              wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Many independent sets in one persistent launch. Set s is
+ * points[offsets[s] .. offsets[s+1]) (each set sorted on its own); its
+ * corners, as indices local to the set, go to out_idx[offsets[s] ...] and
+ * their count to out_counts[s]. Sets are binned by size on the device: a warp,
+ * a CTA or several CTAs per set.
+ * offsets   device int64[num_sets + 1], non-decreasing, offsets[0] >= 0
+ * h_offsets host copy of the same offsets (only read by the size query)
+ * out_idx   device int32[max(offsets[num_sets], 1)], CSR-aligned with points
+ * out_counts device int32[max(num_sets, 1)]
+ * num_sets  >= 0; empty sets are allowed (count 0)
+ * ---------------------------------------------------------------------- */
+size_t wg_upper_hood_batched_workspace_size(const int64_t *h_offsets,
+                                            int32_t num_sets);
+wg_status wg_upper_hood_batched(const float *points, const int64_t *offsets,
+                                int32_t num_sets, int32_t *out_idx,
+                                int32_t *out_counts, void *workspace,
+                                size_t ws_bytes, const wg_options *opts,
+                                wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * End to end from host memory: copies points (host, ideally pinned) to the
+ * caller's device buffer d_points, runs wg_upper_hood_ex, and copies the count
+ * and the corners back to h_out_idx / h_out_count. Synchronises `stream`.
+ * d_out_idx: device int32[max(n,1)]; d_out_count: device int32[1].
+ * ---------------------------------------------------------------------- */
+wg_status wg_upper_hood_from_host(const float *h_points, int64_t n,
+                                  int32_t *h_out_idx, int32_t *h_out_count,
+                                  float *d_points, int32_t *d_out_idx,
+                                  int32_t *d_out_count, void *workspace,
+                                  size_t ws_bytes, const wg_options *opts,
+                                  wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics.
+ * wg_get_device_status: synchronises `stream`, returns the first error the
+ * device recorded in `workspace` since the last read (WG_OK if none) and
+ * clears it.
+ * wg_read_counters: synchronises `stream`; returns the orientation tests and
+ * float64 fallbacks counted by calls made with count_predicates = 1 since the
+ * last read, and clears them.
+ * ---------------------------------------------------------------------- */
+wg_status wg_get_device_status(void *workspace, wg_stream_t stream);
+wg_status wg_read_counters(void *workspace, uint64_t *tests,
+                           uint64_t *fallbacks, wg_stream_t stream);
+const char *wg_status_string(wg_status status);
+
+/* ------------------------------------------------------------------------
+ * Autotuner: times every tile configuration and segment count on the
+ * caller's input (which must be a valid input for wg_upper_hood), keeps the
+ * fastest for this device and the size bucket of n, and writes it to *best.
+ * Later calls with tile_config = 0 use the kept choice for that bucket.
+ * Synchronises `stream`; runs each candidate a few times.
+ * ---------------------------------------------------------------------- */
+wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx,
+                      int32_t *out_count, void *workspace, size_t ws_bytes,
+                      wg_options *best, wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Unit entry points for tests (small sizes; one warp or one CTA).
+ * wg_debug_orient: signs[t] = sign(det(p[3t+1] - p[3t], p[3t+2] - p[3t]))
+ *   for t < ntri (points device float pairs, signs device int8), plus the
+ *   number of float64 fallbacks taken, added to *d_fallbacks (device uint64).
+ *   The paper's left_of (Section 2) is signs[t] > 0.
+ * wg_debug_bridge: the bridge of two hoods P (hp corners) and Q (hq corners),
+ *   P entirely left of Q, each a strictly convex upper chain: writes
+ *   d_pq[0] = p, d_pq[1] = q with H(P u Q) = P[0..p] ++ Q[q..] (Section 2,
+ *   mam 1-5). hp, hq >= 1.
+ * wg_debug_warp_hood: the hood of m <= 32 sorted distinct points computed by
+ *   one warp in registers (stages d = 1..16 of the schedule); writes the
+ *   corner positions to d_out[0..h) and h to d_out_count.
+ * ---------------------------------------------------------------------- */
+wg_status wg_debug_orient(const float *points, int64_t ntri, int8_t *signs,
+                          uint64_t *d_fallbacks, int32_t pred_mode,
+                          wg_stream_t stream);
+wg_status wg_debug_bridge(const float *P, int32_t hp, const float *Q,
+                          int32_t hq, int32_t *d_pq, int32_t pred_mode,
+                          wg_stream_t stream);
+wg_status wg_debug_warp_hood(const float *points, int32_t m, int32_t *d_out,
+                             int32_t *d_out_count, int32_t pred_mode,
+                             wg_stream_t stream);
+
+/* Test hook for the bounded device waits: with stall_ns > 0, every CTA of
+ * later fused calls on this workspace first waits at most stall_ns
+ * nanoseconds on a barrier that nothing completes, records WG_ERR_TIMEOUT and
+ * exits (no output is written). 0 turns the hook off. Synchronises `stream`.
+ * The paper has no counterpart; it exists so that the timeout path can be
+ * tested without hanging or faulting a GPU. */
+wg_status wg_debug_set_stall(void *workspace, int32_t stall_ns, wg_stream_t stream);
+
+/* Library version string. */
+const char *wg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WG_H_ */

@@ -1,0 +1,353 @@
+"""GPU parity: every path through the C ABI against the CPU oracle, element by
+element (corner index lists must be identical; the path is exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_5004_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wg():
+    import __graft_entry__ as g
+    g.build_library()
+    from paper_1203_5004_gb300 import wagener
+    wagener.load()
+    return wagener
+
+
+DEV = "cuda"
+TILE_POINTS = {1: 256 * 17, 2: 256 * 9, 3: 512 * 9}
+
+
+def gpu_points(ps):
+    return torch.from_numpy(ps.points()).to(DEV)
+
+
+def assert_same(got, ref, what=""):
+    got = np.asarray(got)
+    if not np.array_equal(got, ref):
+        n = min(len(got), len(ref))
+        bad = np.nonzero(got[:n] != ref[:n])[0]
+        first = int(bad[0]) if bad.size else n
+        raise AssertionError(f"{what}: {len(got)} vs {len(ref)} corners, first difference at {first}: "
+                             f"gpu {got[first:first + 5].tolist()} oracle {ref[first:first + 5].tolist()}")
+
+
+# ---------------------------------------------------------------- predicate
+def _near_collinear(r, n):
+    o = r.integers(0, inputs.G // 2, size=(n, 2))
+    d = r.integers(-(1 << 10), 1 << 10, size=(n, 2))
+    k = r.integers(1, 1 << 10, size=(n, 1))
+    m = r.integers(1, 1 << 10, size=(n, 1))
+    eps = r.integers(-1, 2, size=(n, 2))
+    a = o + k * d
+    b = o + m * d + eps
+    pts = np.stack([o, a, b], axis=1).reshape(-1, 2)
+    return np.clip(pts, 0, inputs.G - 1).astype(np.int32)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_orient_signs(wg, mode):
+    r = np.random.default_rng(1)
+    rand = r.integers(0, inputs.G, size=(3 * 200_000, 2)).astype(np.int32)
+    near = _near_collinear(r, 200_000)
+    # thin tiles: all three points within a few grid units of a long line
+    pts = np.concatenate([rand, near])
+    ref = oracle.orient_signs(pts[:, 0], pts[:, 1])
+    t = torch.from_numpy(inputs.to_float_points(pts[:, 0], pts[:, 1])).to(DEV)
+    signs, fb = wg.debug_orient(t, pred_mode=mode)
+    assert_same(signs.cpu().numpy(), ref, "orient signs")
+    if mode == 0:
+        assert fb > 0  # the near-collinear triples must reach the float64 path
+        assert fb < ref.shape[0]
+
+
+# ---------------------------------------------------------------- bridge
+def _hood_pair(r, n, span, kind):
+    kx = r.integers(0, span, size=n) * (inputs.G // span if kind == "coarse" else 1)
+    ky = r.integers(0, inputs.G, size=n) if kind != "coarse" else r.integers(0, span, size=n) * (inputs.G // span)
+    kx, ky = inputs.sort_lex(kx, ky)
+    key = kx.astype(np.int64) * inputs.G + ky
+    _, first = np.unique(key, return_index=True)
+    kx, ky = kx[first], ky[first]
+    if kx.shape[0] < 2:
+        return None
+    k = int(r.integers(1, kx.shape[0]))
+    hp = oracle.upper_hull(kx[:k], ky[:k])
+    hq = oracle.upper_hull(kx[k:], ky[k:]) + k
+    return kx, ky, hp, hq
+
+
+@pytest.mark.parametrize("kind", ["fine", "coarse"])
+def test_bridge_against_oracle(wg, kind):
+    r = np.random.default_rng(2 if kind == "fine" else 3)
+    checked = 0
+    for trial in range(400):
+        n = int(r.integers(2, 3000))
+        span = int(r.integers(2, 64)) if kind == "coarse" else inputs.G
+        pair = _hood_pair(r, n, span, kind)
+        if pair is None:
+            continue
+        kx, ky, hp, hq = pair
+        ref = oracle.bridge(kx[hp], ky[hp], kx[hq], ky[hq])
+        P = torch.from_numpy(inputs.to_float_points(kx[hp], ky[hp])).to(DEV)
+        Q = torch.from_numpy(inputs.to_float_points(kx[hq], ky[hq])).to(DEV)
+        got = wg.debug_bridge(P, Q)
+        assert got == ref, (trial, got, ref, len(hp), len(hq))
+        checked += 1
+    assert checked > 300
+
+
+def test_warp_hood_against_oracle(wg):
+    r = np.random.default_rng(4)
+    for trial in range(1500):
+        m = int(r.integers(0, 33))
+        span = int(r.choice([4, 16, 1 << 12, inputs.G]))
+        kx = r.integers(0, span, size=m) * (inputs.G // span)
+        ky = r.integers(0, span, size=m) * (inputs.G // span)
+        kx, ky = inputs.sort_lex(kx, ky)
+        key = kx.astype(np.int64) * inputs.G + ky
+        _, first = np.unique(key, return_index=True)
+        kx, ky = kx[first], ky[first]
+        ref = oracle.upper_hull(kx, ky)
+        t = torch.from_numpy(inputs.to_float_points(kx, ky)).to(DEV) if kx.shape[0] else \
+            torch.empty((0, 2), dtype=torch.float32, device=DEV)
+        got = wg.debug_warp_hood(t)
+        assert_same(got, ref, f"warp hood trial {trial}")
+
+
+# ---------------------------------------------------------------- whole path
+KINDS = ["uniform", "arc", "band", "gauss_x", "columns", "duplicates"]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_small_n_sweep(wg, kind):
+    ws = wg.new_workspace(wg.workspace_size(1000))
+    for n in range(0, 301):
+        ps = inputs.make(kind, n, 100 + n)
+        got = wg.upper_hood(gpu_points(ps), workspace=ws).cpu().numpy() if n else \
+            wg.upper_hood(torch.empty((0, 2), dtype=torch.float32, device=DEV), workspace=ws).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"{kind} n={n}")
+    assert wg.device_status(ws) == 0
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("kind", KINDS)
+def test_tile_edges(wg, cfg, kind):
+    T = TILE_POINTS[cfg]
+    opts = wg.default_options(tile_config=cfg)
+    ws = wg.new_workspace(wg.workspace_size(1 << 22))
+    for n in (T - 1, T, T + 1, 2 * T - 1, 3 * T + 7, 17 * T + 5, 200 * T + 3):
+        ps = inputs.make(kind, n, n)
+        got = wg.upper_hood(gpu_points(ps), opts=opts, workspace=ws).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"cfg{cfg} {kind} n={n}")
+    assert wg.device_status(ws) == 0
+
+
+@pytest.mark.parametrize("k", list(range(1, 22)))
+def test_powers_of_two(wg, k):
+    for n in (2 ** k - 1, 2 ** k, 2 ** k + 1):
+        ps = inputs.uniform(n, k)
+        got = wg.upper_hood(gpu_points(ps)).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"uniform n={n}")
+
+
+@pytest.mark.parametrize("spc", [1, 2, 4, 8])
+def test_segments_per_cta(wg, spc):
+    ps = inputs.band(3_000_000, 9)
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    for cfg in (1, 2, 3):
+        got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(tile_config=cfg, segments_per_cta=spc))
+        assert_same(got.cpu().numpy(), ref, f"cfg{cfg} spc{spc}")
+
+
+def test_closed_form_all_corners(wg):
+    ps = inputs.closed_form()
+    got = wg.upper_hood(gpu_points(ps)).cpu().numpy()
+    assert_same(got, np.arange(4096, dtype=np.int32), "closed form")
+
+
+def test_unaligned_points(wg):
+    # a view that starts 8 bytes past a 16-byte boundary: every tile is staged
+    # with a one-point shift
+    for kind in ("uniform", "band", "duplicates"):
+        ps = inputs.make(kind, 1_000_001, 5)
+        base = torch.zeros((len(ps) + 1, 2), dtype=torch.float32, device=DEV)
+        base[1:] = gpu_points(ps)
+        view = base[1:]
+        assert view.data_ptr() % 16 == 8
+        got = wg.upper_hood(view).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"unaligned {kind}")
+
+
+def test_long_hood_spills_window(wg):
+    # Every point of a long strictly concave chain is a corner: the running
+    # hood outgrows its shared window and spills to the output array.
+    # y = i (N - i) / 2 (exact: N is odd) has second difference -1: every
+    # point is a corner.
+    N = 11583
+    i = np.arange(N + 1, dtype=np.int64)
+    kx = i * 1448
+    ky = i * (N - i) // 2
+    ps = inputs.PointSet(kx, ky)
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    assert ref.shape[0] == N + 1
+    for cfg in (1, 2, 3):
+        got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(tile_config=cfg)).cpu().numpy()
+        assert_same(got, ref, f"concave chain cfg{cfg}")
+
+
+@pytest.mark.parametrize("name,make", [
+    ("2^16 uniform", lambda: inputs.uniform(1 << 16, 1)),
+    ("2^24 uniform", lambda: inputs.uniform(1 << 24, 2)),
+    ("2^24 arc", lambda: inputs.arc(1 << 24, 3)),
+    ("2^26 uniform", lambda: inputs.uniform(1 << 26, 7)),
+])
+def test_configs(wg, name, make):
+    ps = make()
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    got = wg.upper_hood(gpu_points(ps)).cpu().numpy()
+    assert_same(got, ref, name)
+
+
+def test_band_2_26_filtered_and_fp64(wg):
+    ps = inputs.band(1 << 26, 4)
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    for mode in (0, 1):
+        o = wg.default_options(pred_mode=mode, count_predicates=1)
+        out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+        cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+        wg.upper_hood_into(pts, out, cnt, ws, o)
+        got = out[: int(cnt.item())].cpu().numpy()
+        assert_same(got, ref, f"band 2^26 mode {mode}")
+        tests, fb = wg.read_counters(ws)
+        assert tests > 0
+        if mode == 0:
+            assert 0 < fb < tests
+        else:
+            assert fb == 0
+    assert wg.device_status(ws) == 0
+
+
+@pytest.mark.slow
+def test_gauss_x_2_28(wg):
+    ps = inputs.gauss_x(1 << 28, 6)
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    pts = gpu_points(ps)
+    del ps
+    got = wg.upper_hood(pts).cpu().numpy()
+    assert_same(got, ref, "gauss_x 2^28 fused")
+    got = wg.upper_hood_plain(pts).cpu().numpy()
+    assert_same(got, ref, "gauss_x 2^28 plain")
+
+
+# ---------------------------------------------------------------- plain path
+@pytest.mark.parametrize("kind", KINDS)
+def test_plain_schedule(wg, kind):
+    for n in (1, 2, 3, 5, 64, 1000, 4097, 100_003, 1 << 20):
+        ps = inputs.make(kind, n, n + 1)
+        got = wg.upper_hood_plain(gpu_points(ps)).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"plain {kind} n={n}")
+
+
+def test_plain_long_chain(wg):
+    ps = inputs.closed_form()
+    assert_same(wg.upper_hood_plain(gpu_points(ps)).cpu().numpy(), np.arange(4096, dtype=np.int32), "plain 2c")
+
+
+# ---------------------------------------------------------------- batched
+@pytest.mark.parametrize("num_sets,hi", [(1, 100), (50, 3000), (3000, 65536)])
+def test_batched(wg, num_sets, hi):
+    ps, offs, _ = inputs.batched(num_sets, seed=5 + num_sets, hi=hi)
+    ref_out, ref_cnt = oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    out, cnt = wg.upper_hood_batched(gpu_points(ps), offs)
+    out, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+    assert_same(cnt, ref_cnt, "batched counts")
+    for s in range(num_sets):
+        a = offs[s]
+        assert_same(out[a:a + cnt[s]], ref_out[a:a + ref_cnt[s]], f"set {s}")
+
+
+def test_batched_with_empty_and_large_sets(wg):
+    sizes = [0, 1, 2, 0, 5, 300_000, 0, 7, 1_000_000, 3]
+    sets = [inputs.make(k, n, i) for i, (k, n) in enumerate(zip(
+        ["uniform", "band", "arc", "uniform", "duplicates", "band", "arc", "columns", "gauss_x", "uniform"], sizes))]
+    kx = np.concatenate([s.kx for s in sets])
+    ky = np.concatenate([s.ky for s in sets])
+    offs = np.zeros(len(sizes) + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    ref_out, ref_cnt = oracle.upper_hull_batched(kx, ky, offs)
+    pts = torch.from_numpy(inputs.to_float_points(kx, ky)).to(DEV)
+    for rep in range(2):
+        out, cnt = wg.upper_hood_batched(pts, offs)
+        out, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+        assert_same(cnt, ref_cnt, "counts")
+        for s in range(len(sizes)):
+            a = offs[s]
+            assert_same(out[a:a + cnt[s]], ref_out[a:a + ref_cnt[s]], f"set {s}")
+
+
+# ---------------------------------------------------------------- options
+def test_validation_reports(wg):
+    ps = inputs.uniform(100_000, 3)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    o = wg.default_options(validate=1)
+    out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    wg.upper_hood_into(pts, out, cnt, ws, o)
+    assert wg.device_status(ws) == 0
+    bad = pts.clone()
+    bad[[7000, 7001]] = bad[[7001, 7000]]
+    wg.upper_hood_into(bad, out, cnt, ws, o)
+    assert wg.device_status(ws) == 3
+    bad = pts.clone()
+    # 0.3 in float32 is a multiple of 2^-24; one more 2^-25 is off the grid
+    # but still below the next grid value, so the order is unchanged.
+    bad[9000, 1] = float(np.float32(0.3) + np.float32(2.0 ** -25))
+    wg.upper_hood_into(bad, out, cnt, ws, o)
+    assert wg.device_status(ws) == 4
+
+
+def test_timeout_hook(wg):
+    ps = inputs.uniform(200_000, 3)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    wg.debug_set_stall(ws, 2_000_000)  # 2 ms bounded wait that nothing ends
+    out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    wg.upper_hood_into(pts, out, cnt, ws)
+    assert wg.device_status(ws) == 5
+    wg.debug_set_stall(ws, 0)
+    got = wg.upper_hood(pts, workspace=ws).cpu().numpy()
+    assert_same(got, oracle.upper_hull(ps.kx, ps.ky), "after timeout")
+    assert wg.device_status(ws) == 0
+
+
+def test_from_host(wg):
+    ps = inputs.uniform(1 << 20, 8)
+    n = len(ps)
+    h_pts = ps.points()
+    d_pts = torch.empty((n, 2), dtype=torch.float32, device=DEV)
+    d_out = torch.empty(n, dtype=torch.int32, device=DEV)
+    d_cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    ws = wg.new_workspace(wg.workspace_size(n))
+    h_out = np.empty(n, dtype=np.int32)
+    h = wg.upper_hood_from_host(h_pts, d_pts, d_out, d_cnt, ws, h_out)
+    assert_same(h_out[:h], oracle.upper_hull(ps.kx, ps.ky), "from host")
+
+
+def test_autotune_keeps_results(wg):
+    ps = inputs.uniform(1 << 22, 12)
+    pts = gpu_points(ps)
+    best = wg.autotune(pts)
+    assert 1 <= best.tile_config <= 3
+    got = wg.upper_hood(pts).cpu().numpy()
+    assert_same(got, oracle.upper_hull(ps.kx, ps.ky), "after autotune")
