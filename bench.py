@@ -1,0 +1,343 @@
+"""Benchmark of the upper-hood path on GB300 (prints one JSON line).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload uniform26|uniform24|arc24|band26|gauss28|uniform16|closed4096|batched]
+
+A step is one pass of the whole path over one input: one call of
+wg_upper_hood on a device-resident set (one fused kernel launch). The default
+workload is one set of 2^26 points uniform on the 2^-24 grid (537 MB, larger
+than the 129 MB L2, so no flush is needed between steps).
+
+value      = points processed by all ranks / (max over ranks of the timed
+             region), Gpoints/s, timed with CUDA events on the launching
+             stream around K steps after W warm-up steps.
+e2e        = the same metric through wg_upper_hood_from_host: pinned host
+             points copied in, corners and count copied out, every step.
+roofline   = algorithmic bytes (8n in + 4h + 4 out) per launch / average
+             launch time, against the measured HBM copy bandwidth.
+cpu_baseline = the CPU oracle (monotone chain, one core) on the same input.
+
+Under torchrun (N > 1) every rank hulls its own set of the same size (weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "upper-hull Gpoints/s and % HBM roofline; batched sets/s vs plain per-set"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "uniform26": ("uniform", 1 << 26, 7, "uniform n=2^26 single set (north-star target)"),
+    "uniform24": ("uniform", 1 << 24, 2, "uniform n=2^24 single set"),
+    "arc24": ("arc", 1 << 24, 3, "arc y=1-4(x-1/2)^2 n=2^24 single set"),
+    "band26": ("band", 1 << 26, 4, "parabola band 2^-20 wide n=2^26 single set"),
+    "gauss28": ("gauss_x", 1 << 28, 6, "gaussian-x n=2^28 single set"),
+    "uniform16": ("uniform", 1 << 16, 1, "uniform n=2^16 single set"),
+    "closed4096": ("closed_form", 4096, 0, "closed form x=i/4096, y=i(4095-i)/2^24"),
+}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1203_5004_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(workload: str):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", f"fused_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        ident = str(self.dev)
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", ident], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_input(kind: str, n: int, seed: int):
+    from paper_1203_5004_gb300 import inputs
+    return inputs.make(kind, n, seed)
+
+
+def time_oracle(ps, budget_s: float = 12.0, max_reps: int = 20):
+    """The CPU oracle as it stands, one core, repeated on the full input."""
+    import oracle
+    oracle.upper_hull(ps.kx[:1000], ps.ky[:1000])  # build + load outside the timing
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.upper_hull(ps.kx, ps.ky)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= max_reps:
+            break
+    return len(ps) * reps / el / 1e9, reps, el
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle timed as the step, on this workload."""
+    if rank != 0:
+        return
+    kind, n, seed, desc = WORKLOADS[args.workload]
+    ps = make_input(kind, n, seed)
+    import oracle
+    oracle.upper_hull(ps.kx[:1000], ps.ky[:1000])
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.upper_hull(ps.kx, ps.ky)
+    steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.upper_hull(ps.kx, ps.ky)
+    el = time.perf_counter() - t0
+    value = n * steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "seed": seed},
+        "cpu_baseline": {"value": value, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full input, {steps} runs of the single-thread monotone chain"},
+        "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1203_5004_gb300 import wagener
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    kind, n, seed, desc = WORKLOADS[args.workload]
+    ps = make_input(kind, n, seed + 1000 * rank if rank else seed)
+    pts = torch.from_numpy(ps.points()).to(dev)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = wagener.new_workspace(wagener.workspace_size(n), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    opts = wagener.autotune(pts, workspace=ws) if not args.no_autotune else wagener.default_options()
+    for _ in range(max(3, args.warmup)):
+        wagener.upper_hood_into(pts, out, cnt, ws, opts)
+    torch.cuda.synchronize(dev)
+    h = int(cnt.item())
+    if wagener.device_status(ws) != 0:
+        raise RuntimeError("device reported an error during warm-up")
+
+    K = args.steps
+    if args.profile:
+        # Launch list / counter capture: the timed steps only, nothing else.
+        for _ in range(K):
+            wagener.upper_hood_into(pts, out, cnt, ws, opts)
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "workload": desc, "n": n, "steps": K, "hull_corners": h}))
+        if pg:
+            pg.destroy_process_group()
+        return
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(K):
+        starts[i].record(stream)
+        wagener.upper_hood_into(pts, out, cnt, ws, opts)
+        ends[i].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
+    if wagener.device_status(ws) != 0:
+        raise RuntimeError("device reported an error in the timed region")
+    ms = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(ms, op=pg.ReduceOp.MAX)
+    total_ms = float(ms.item())
+    value = n * world * K / (total_ms * 1e-3) / 1e9
+
+    # End to end through the public host-buffer entry point.
+    h_pts = torch.from_numpy(ps.points()).pin_memory().numpy()
+    h_out = torch.empty(max(n, 1), dtype=torch.int32).pin_memory().numpy()
+    e2e_steps = max(1, min(K, 10))
+    for _ in range(2):
+        wagener.upper_hood_from_host(h_pts, pts, out, cnt, ws, h_out, opts)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        hh = wagener.upper_hood_from_host(h_pts, pts, out, cnt, ws, h_out, opts)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - te
+    es = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if pg:
+        pg.all_reduce(es, op=pg.ReduceOp.MAX)
+    e2e_s = float(es.item())
+    e2e_value = n * world * e2e_steps / e2e_s / 1e9
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak()
+    alg_bytes = 8 * n + 4 * h + 4
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+    cpu_gpts, reps, el = time_oracle(ps)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "seed": seed, "hull_corners": h,
+                   "tile_config": int(opts.tile_config), "segments_per_cta": int(opts.segments_per_cta),
+                   "l2": "input 8n bytes > 129 MB L2 (no flush)" if 8 * n > 129e6 else "input fits L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "fused_kernel", "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 4 + 4 * hh},
+        "gpu_launches": K,
+        "clocks": clocks,
+        "cpu_baseline": {"value": cpu_gpts, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full input, {reps} runs of the single-thread monotone chain, {el:.1f} s"},
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up and the K steps (for ncu); prints no bench line")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -80,7 +80,7 @@ typedef struct wg_options {
     int32_t reserved[3];
 } wg_options;
 
-#define WG_NUM_TILE_CONFIGS 3
+#define WG_NUM_TILE_CONFIGS 4
 
 /* Fills *opts with the defaults (filtered predicate, no counters, no
  * validation, library-chosen tiling). */

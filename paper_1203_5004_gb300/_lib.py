@@ -19,7 +19,7 @@ STATUS_NAMES = {
 }
 WG_PRED_FILTERED = 0
 WG_PRED_FP64 = 1
-NUM_TILE_CONFIGS = 3
+NUM_TILE_CONFIGS = 4
 
 # Every function the header declares, with (restype, argtypes).
 _vp = ctypes.c_void_p

@@ -16,6 +16,7 @@ namespace wg {
 cudaError_t fused_launch(int cfg, const FusedArgs &args, int grid, int mode, cudaStream_t stream);
 cudaError_t fused_occupancy(int cfg, int *blocks);
 int fused_tile_points(int cfg);
+int fused_warps(int cfg);
 size_t fused_smem_bytes(int cfg);
 cudaError_t plain_stage_launch(const PlainArgs &a, bool first, int mode, cudaStream_t st);
 long long plain_blocks(long long hoods);
@@ -34,10 +35,16 @@ using namespace wg;
 
 namespace {
 
-constexpr int kMaxSeg = 2048;        // segments of one fused call
-constexpr size_t kOffArrivals = 256;  // after the header
+// Single-set workspace: header | arrivals | per segment: count, max y,
+// final-merge scratch (4 ints), staged hood coordinates (kStageCorners).
+constexpr int kMaxSeg = 4096;        // segments (warp streams) of one fused call
+constexpr size_t kOffArrivals = 256;
 constexpr size_t kOffSegCount = 512;
-constexpr int kDefaultCfg = 2;
+constexpr size_t kOffSegYmax = kOffSegCount + 4 * kMaxSeg;
+constexpr size_t kOffSegLive = kOffSegYmax + 4 * kMaxSeg;
+constexpr size_t kOffSegXy = kOffSegLive + 16 * kMaxSeg + 16;
+constexpr size_t kSingleWsBytes = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
+constexpr int kDefaultCfg = 1;
 
 struct DevInfo {
     bool init = false;
@@ -151,7 +158,7 @@ const char *wg_status_string(wg_status s)
 size_t wg_upper_hood_workspace_size(int64_t n)
 {
     (void)n;
-    return kOffSegCount + sizeof(int) * kMaxSeg;
+    return kSingleWsBytes;
 }
 
 wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
@@ -178,12 +185,16 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
         if (cfg == 0) cfg = t.cfg ? t.cfg : kDefaultCfg;
         if (spc == 0) spc = t.spc ? t.spc : 1;
     }
+    // One segment of whole tiles per warp stream; segments_per_cta > 1 only
+    // shortens segments (more CTAs than fit at once), it never gives a warp
+    // two segments.
     const int T = fused_tile_points(cfg);
+    const int W = fused_warps(cfg);
     const long long tiles = (n + T - 1) / T;
     const int resident = std::max(1, d->occ[cfg]) * d->sms;
-    long long nseg = std::min<long long>(tiles, (long long)resident * spc);
-    nseg = std::min<long long>(nseg, std::min(kMaxSeg, T));
-    const int grid = (int)std::min<long long>(nseg, resident);
+    long long nseg = std::min<long long>(tiles, (long long)resident * W * spc);
+    nseg = std::min<long long>(nseg, kMaxSeg);
+    const int grid = (int)((nseg + W - 1) / W);
 
     FusedArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -198,6 +209,9 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     a.hdr = reinterpret_cast<WsHeader *>(workspace);
     a.arrivals = reinterpret_cast<unsigned *>(static_cast<char *>(workspace) + kOffArrivals);
     a.seg_count = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffSegCount);
+    a.seg_ymax = reinterpret_cast<float *>(static_cast<char *>(workspace) + kOffSegYmax);
+    a.seg_live = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffSegLive);
+    a.seg_xy = reinterpret_cast<float *>(static_cast<char *>(workspace) + kOffSegXy);
     if (fused_launch(cfg, a, grid, pred_mode_bits(o), S(stream)) != cudaSuccess) return WG_ERR_CUDA;
     return WG_OK;
 }

@@ -20,19 +20,22 @@ cudaError_t fused_launch(int cfg, const FusedArgs &args, int grid, int mode, cud
 cudaError_t fused_occupancy(int cfg, int *blocks);
 int fused_tile_points(int cfg);
 
-constexpr int kMaxTilesPerSeg = 64;
+constexpr int kMaxTilesPerSeg = 128;
 constexpr int kMaxSegPerSet = 2048;  // the final merge keeps 2 ints per segment in one tile buffer
 constexpr int kPlanThreads = 1024;
 constexpr int kBins = 3;
 
 struct BatchLayout {
-    size_t arrivals, seg_count, items, ctl, total;
-    long long max_items;
+    size_t arrivals, seg_count, seg_ymax, items, stage_xy, stage_live, ctl, total;
+    long long max_items, max_stage;
 };
 
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-static BatchLayout batch_layout(int num_sets, long long max_items)
+// header | arrivals (per set) | per item: count, max y, the item itself |
+// per stage slot (segments of multi-segment sets take one each): staged hood
+// coordinates, final-merge scratch | control words.
+static BatchLayout batch_layout(int num_sets, long long max_items, long long max_stage)
 {
     BatchLayout L;
     size_t o = 256;
@@ -40,19 +43,26 @@ static BatchLayout batch_layout(int num_sets, long long max_items)
     o = align256(o + (size_t)std::max(num_sets, 1) * 4);
     L.seg_count = o;
     o = align256(o + (size_t)std::max<long long>(max_items, 1) * 4);
+    L.seg_ymax = o;
+    o = align256(o + (size_t)std::max<long long>(max_items, 1) * 4);
     L.items = o;
     o = align256(o + (size_t)std::max<long long>(max_items, 1) * sizeof(SegItem));
-    L.ctl = o;  // num_items, queue, done, bin cursors
+    L.stage_xy = o;
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 8 * kStageCorners);
+    L.stage_live = o;
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 16 + 16);
+    L.ctl = o;  // num_items, queue, done, bounds
     o = align256(o + 64);
     L.total = o;
     L.max_items = max_items;
+    L.max_stage = max_stage;
     return L;
 }
 
 static int min_tile_points()
 {
     int t = 1 << 30;
-    for (int c = 1; c <= kNumTileCfgs; ++c) t = std::min(t, kTileCfgs[c - 1].threads * kTileCfgs[c - 1].k);
+    for (int c = 1; c <= kNumTileCfgs; ++c) t = std::min(t, 32 * kTileCfgs[c - 1].k);
     return t;
 }
 
@@ -64,21 +74,24 @@ size_t batched_workspace_bytes(const int64_t *h_offsets, int num_sets)
         const long long n = h_offsets[s + 1] - h_offsets[s];
         if (n <= 0) continue;
         const long long tiles = (n + T - 1) / T;
-        items += std::min<long long>((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, kMaxSegPerSet);
+        const long long ns = std::min<long long>((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, kMaxSegPerSet);
+        items += ns;
     }
-    return batch_layout(num_sets, items).total;
+    return batch_layout(num_sets, items, items).total;
 }
 
 __device__ __forceinline__ int bin_of(long long tiles) { return tiles >= 8 ? 0 : (tiles >= 2 ? 1 : 2); }
 
 __global__ void __launch_bounds__(kPlanThreads)
     batch_plan_kernel(const int64_t *off, int num_sets, int T, SegItem *items, long long max_items,
-                      int *ctl, int32_t *out_counts, int *status)
+                      long long max_stage, int *ctl, int32_t *out_counts, int *status)
 {
     __shared__ int s_bin[kBins];
     __shared__ int s_cur[kBins];
+    __shared__ int s_stage;
     const int tid = threadIdx.x;
     if (tid < kBins) s_bin[tid] = 0;
+    if (tid == 0) s_stage = 0;
     __syncthreads();
     for (int s = tid; s < num_sets; s += kPlanThreads) {
         const long long n = off[s + 1] - off[s];
@@ -113,6 +126,14 @@ __global__ void __launch_bounds__(kPlanThreads)
         const long long tiles = (n + T - 1) / T;
         const int nseg = (int)min((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, (long long)kMaxSegPerSet);
         const int base = atomicAdd(&s_cur[bin_of(tiles)], nseg);
+        int stage = 0;
+        if (nseg > 1) {
+            stage = atomicAdd(&s_stage, nseg);
+            if (stage + nseg > max_stage) {
+                atomicCAS(status, 0, 2);
+                stage = 0;
+            }
+        }
         for (int c = 0; c < nseg; ++c) {
             SegItem it;
             const long long lo = (long long)c * tiles / nseg, hi = (long long)(c + 1) * tiles / nseg;
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(kPlanThreads)
             it.nseg = nseg;
             it.slot = base + c;
             it.slot0 = base;
-            it.pad = 0;
+            it.pad = stage + c;
             items[base + c] = it;
         }
     }
@@ -134,22 +155,23 @@ cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_
                            int32_t *out_counts, void *ws, size_t ws_bytes, int cfg, int mode, int validate,
                            cudaStream_t st)
 {
-    // The item bound of the workspace: recover it from its size.
+    // The item bound of the workspace, recovered from its size (every item
+    // has a stage slot, so one bound sizes everything).
     long long lo = 0, hi = 1;
-    while (batch_layout(num_sets, hi).total <= ws_bytes && hi < (1ll << 40)) hi *= 2;
+    while (batch_layout(num_sets, hi, hi).total <= ws_bytes && hi < (1ll << 40)) hi *= 2;
     while (lo + 1 < hi) {
         const long long mid = (lo + hi) / 2;
-        if (batch_layout(num_sets, mid).total <= ws_bytes) lo = mid; else hi = mid;
+        if (batch_layout(num_sets, mid, mid).total <= ws_bytes) lo = mid; else hi = mid;
     }
-    if (lo < 1 || batch_layout(num_sets, lo).total > ws_bytes) return cudaErrorInvalidValue;
-    const BatchLayout L = batch_layout(num_sets, lo);
+    if (lo < 1 || batch_layout(num_sets, lo, lo).total > ws_bytes) return cudaErrorInvalidValue;
+    const BatchLayout L = batch_layout(num_sets, lo, lo);
     char *w = static_cast<char *>(ws);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(w);
     int *ctl = reinterpret_cast<int *>(w + L.ctl);
     SegItem *items = reinterpret_cast<SegItem *>(w + L.items);
     const int T = fused_tile_points(cfg);
-    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(offsets, num_sets, T, items, L.max_items, ctl, out_counts,
-                                                  &hdr->status);
+    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(offsets, num_sets, T, items, L.max_items, L.max_stage, ctl,
+                                                  out_counts, &hdr->status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
@@ -171,6 +193,9 @@ cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_
     a.validate = validate;
     a.hdr = hdr;
     a.seg_count = reinterpret_cast<int *>(w + L.seg_count);
+    a.seg_ymax = reinterpret_cast<float *>(w + L.seg_ymax);
+    a.seg_xy = reinterpret_cast<float *>(w + L.stage_xy);
+    a.seg_live = reinterpret_cast<int *>(w + L.stage_live);
     a.arrivals = reinterpret_cast<unsigned *>(w + L.arrivals);
     const int grid = std::max(1, blocks) * sms;
     return fused_launch(cfg, a, grid, mode, st);

@@ -167,15 +167,17 @@ __device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int
 {
     const int lane = lane_id();
     int lo = 0, hi = hp - 1;  // invariant: lo <= p* <= hi and !fLOW(hi)
+    int thi = -1;             // tangent corner from P[hi], once a probe found it
     while (lo < hi) {
         const int span = hi - lo;
         const int step = (span + 31) >> 5;
         const int i = lo + lane * step;
         const bool valid = i < hi;
         bool low = false;
+        int t = 0;
         if (valid) {
             const float2 p = P.pt(i);
-            const int t = tangent_from<MODE>(pc, p, Q, hq);
+            t = tangent_from<MODE>(pc, p, Q, hq);
             low = orient<MODE>(pc, p, Q.pt(t), P.pt(i + 1)) > 0;
         }
         const unsigned vm = __ballot_sync(kFull, valid);
@@ -185,11 +187,12 @@ __device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int
             const int nhi = lo + f * step;
             lo = f > 0 ? lo + (f - 1) * step + 1 : lo;
             hi = nhi;
+            thi = __shfl_sync(kFull, t, f);
         } else {
             lo = lo + (31 - __clz(vm)) * step + 1;
         }
     }
-    const int q = tangent_from<MODE>(pc, P.pt(lo), Q, hq);
+    const int q = thi >= 0 ? thi : tangent_from<MODE>(pc, P.pt(lo), Q, hq);
     return make_int2(lo, q);
 }
 
@@ -210,6 +213,7 @@ __device__ int warp_hood_regs(PredCount &pc, float2 &pt, int &id, int m)
     int cnt = lane < m ? 1 : 0;  // size of the hood of my group
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
+        if (d >= m) break;  // one group left: P holds every point, Q none
         const int g = lane & ~(2 * d - 1);
         const int r = lane - g;
         const int hp = __shfl_sync(kFull, cnt, g);

@@ -13,6 +13,8 @@ cudaError_t fused_occupancy_cfg1(int *blocks) { return occupancy_cfg<Cfg1>(block
 
 int fused_tile_points_cfg1() { return Cfg1::kT; }
 
+int fused_warps_cfg1() { return Cfg1::kW; }
+
 size_t fused_smem_bytes_cfg1() { return Cfg1::kBytes; }
 
 }  // namespace wg

@@ -13,6 +13,8 @@ cudaError_t fused_occupancy_cfg2(int *blocks) { return occupancy_cfg<Cfg2>(block
 
 int fused_tile_points_cfg2() { return Cfg2::kT; }
 
+int fused_warps_cfg2() { return Cfg2::kW; }
+
 size_t fused_smem_bytes_cfg2() { return Cfg2::kBytes; }
 
 }  // namespace wg

@@ -13,6 +13,8 @@ cudaError_t fused_occupancy_cfg3(int *blocks) { return occupancy_cfg<Cfg3>(block
 
 int fused_tile_points_cfg3() { return Cfg3::kT; }
 
+int fused_warps_cfg3() { return Cfg3::kW; }
+
 size_t fused_smem_bytes_cfg3() { return Cfg3::kBytes; }
 
 }  // namespace wg

@@ -26,7 +26,7 @@ struct SegItem {
     int nseg;            // segments of this set
     int slot;            // index of this segment's count in seg_count
     int slot0;           // slot of segment 0 of this set
-    int pad;
+    int pad;             // stage slot (segments of multi-segment sets)
 };
 
 struct FusedArgs {
@@ -45,20 +45,28 @@ struct FusedArgs {
     unsigned *done;            // batched: CTAs finished
     int validate;
     WsHeader *hdr;
-    int *seg_count;          // one per segment
+    int *seg_count;          // one per segment slot (negative: coordinates not staged)
+    float *seg_ymax;         // one per segment slot: max y of the segment
+    float *seg_xy;           // per stage slot: kStageCorners float2 (segment hood coordinates)
+    int *seg_live;           // per stage slot: 4 ints of final-merge scratch (+1)
     unsigned *arrivals;      // one per set
 };
 
-// Tile configurations (threads per CTA, points per thread (odd), pipeline
-// depth, running-hood window). Index 1..kNumTileCfgs as exposed in the ABI.
+// Corners of a segment hood whose coordinates are staged for the final merge
+// (the running window of every tile configuration has this size).
+constexpr int kStageCorners = 128;
+
+// Tile configurations (warps per CTA, points per lane (odd), tile buffers
+// per warp, running window). Index 1..kNumTileCfgs as exposed in the ABI.
 struct TileCfgDesc {
-    int threads, k, stages, rcap;
+    int warps, k, stages, rcap;
 };
-constexpr int kNumTileCfgs = 3;
+constexpr int kNumTileCfgs = 4;
 constexpr TileCfgDesc kTileCfgs[kNumTileCfgs] = {
-    {256, 17, 3, 1024},
-    {256, 9, 4, 1024},
-    {512, 9, 3, 1024},
+    {8, 23, 4, 128},
+    {12, 15, 4, 128},
+    {8, 31, 3, 128},
+    {6, 31, 4, 128},
 };
 
 // Plain full-stage path.

@@ -21,7 +21,7 @@ def wg():
 
 
 DEV = "cuda"
-TILE_POINTS = {1: 256 * 17, 2: 256 * 9, 3: 512 * 9}
+TILE_POINTS = {1: 128 * 31, 2: 128 * 23, 3: 256 * 31, 4: 256 * 15}
 
 
 def gpu_points(ps):
@@ -136,7 +136,7 @@ def test_small_n_sweep(wg, kind):
     assert wg.device_status(ws) == 0
 
 
-@pytest.mark.parametrize("cfg", [1, 2, 3])
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
 @pytest.mark.parametrize("kind", KINDS)
 def test_tile_edges(wg, cfg, kind):
     T = TILE_POINTS[cfg]
@@ -161,7 +161,7 @@ def test_powers_of_two(wg, k):
 def test_segments_per_cta(wg, spc):
     ps = inputs.band(3_000_000, 9)
     ref = oracle.upper_hull(ps.kx, ps.ky)
-    for cfg in (1, 2, 3):
+    for cfg in (1, 2, 3, 4):
         got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(tile_config=cfg, segments_per_cta=spc))
         assert_same(got.cpu().numpy(), ref, f"cfg{cfg} spc{spc}")
 
@@ -197,7 +197,7 @@ def test_long_hood_spills_window(wg):
     ps = inputs.PointSet(kx, ky)
     ref = oracle.upper_hull(ps.kx, ps.ky)
     assert ref.shape[0] == N + 1
-    for cfg in (1, 2, 3):
+    for cfg in (1, 2, 3, 4):
         got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(tile_config=cfg)).cpu().numpy()
         assert_same(got, ref, f"concave chain cfg{cfg}")
 
@@ -348,6 +348,6 @@ def test_autotune_keeps_results(wg):
     ps = inputs.uniform(1 << 22, 12)
     pts = gpu_points(ps)
     best = wg.autotune(pts)
-    assert 1 <= best.tile_config <= 3
+    assert 1 <= best.tile_config <= 4
     got = wg.upper_hood(pts).cpu().numpy()
     assert_same(got, oracle.upper_hull(ps.kx, ps.ky), "after autotune")
