@@ -154,6 +154,21 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank r's set under weak scaling (rank 0 uses the workload's own)."""
+    return seed + 1000 * rank if rank else seed
+
+
 def make_input(kind: str, n: int, seed: int):
     from paper_1203_5004_gb300 import inputs
     return inputs.make(kind, n, seed)
@@ -213,7 +228,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     kind, n, seed, desc = WORKLOADS[args.workload]
-    ps = make_input(kind, n, seed + 1000 * rank if rank else seed)
+    ps = make_input(kind, n, rank_seed(seed, rank))
     pts = torch.from_numpy(ps.points()).to(dev)
     out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     cnt = torch.empty(1, dtype=torch.int32, device=dev)
@@ -263,10 +278,7 @@ def run_ours(args, world, rank, local):
     launch_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
     if wagener.device_status(ws) != 0:
         raise RuntimeError("device reported an error in the timed region")
-    ms = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(ms, op=pg.ReduceOp.MAX)
-    total_ms = float(ms.item())
+    total_ms = max_over_ranks(total_ms, pg, dev)
     value = n * world * K / (total_ms * 1e-3) / 1e9
 
     # End to end through the public host-buffer entry point.
@@ -283,10 +295,7 @@ def run_ours(args, world, rank, local):
         hh = wagener.upper_hood_from_host(h_pts, pts, out, cnt, ws, h_out, opts)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - te
-    es = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if pg:
-        pg.all_reduce(es, op=pg.ReduceOp.MAX)
-    e2e_s = float(es.item())
+    e2e_s = max_over_ranks(e2e_s, pg, dev)
     e2e_value = n * world * e2e_steps / e2e_s / 1e9
 
     if rank != 0:
