@@ -214,6 +214,36 @@ wg_status wg_debug_warp_hood(const float *points, int32_t m, int32_t *d_out,
  * tested without hanging or faulting a GPU. */
 wg_status wg_debug_set_stall(void *workspace, int32_t stall_ns, wg_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * wg_upper_hood_noalloc: the same result as wg_upper_hood, for callers that
+ * must not allocate device memory. The paper has no counterpart; it exists
+ * for callers such as a plugin that runs inside another program's fixed
+ * device-memory budget, a real-time loop that may never block in the
+ * allocator, or code that has nowhere to keep a workspace between calls.
+ *
+ * The caller passes only the input and the outputs (as for wg_upper_hood).
+ * The bookkeeping lives in one fixed array (about 2.2 MB) in this library's
+ * own device memory, which every GPU that loads the library holds until the
+ * process exits. It covers at most 2048 segments, and the call never plans
+ * more, so every n from 0 to 2^31 - 1 fits; a larger n is rejected with
+ * WG_ERR_UNSUPPORTED, a negative n with WG_ERR_INVALID_VALUE.
+ *
+ * - The first call on a device looks up the array's device address (with
+ *   that device current) and keeps it; make that first call before any
+ *   stream capture.
+ * - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ *   routine. Each call clears the part of the array that must start at zero
+ *   with a cudaMemsetAsync on `stream`, then launches the fused kernel.
+ * - All calls in the process share the array. Calls whose GPU work overlaps
+ *   (on different streams, or from different threads) race on it and give
+ *   wrong results; serialise them.
+ * - Only argument and launch errors are reported. Errors found on the device
+ *   (a bounded wait that timed out) are not visible here; use
+ *   wg_upper_hood_ex with a workspace to read them.
+ * ---------------------------------------------------------------------- */
+wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32_t *out_idx,
+                                int32_t *out_count, wg_stream_t stream);
+
 /* Library version string. */
 const char *wg_version(void);
 

@@ -1,0 +1,122 @@
+// wg_noalloc.cu -- wg_upper_hood_noalloc: the fused upper-hood call for
+// callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs under a fixed device
+// memory budget handed out by someone else (a plugin inside a host
+// application, a real-time loop that must never block in the allocator, a
+// process whose memory pool is owned and capped by its host), or code that
+// simply has no way to keep a workspace alive between calls. This entry
+// point needs nothing but the caller's input and output buffers: its
+// bookkeeping lives in one fixed array in the library's own device memory,
+// sized once for the largest plan the fused kernel makes (at most
+// kNoAllocSegments segments).
+//
+// The array is a file-scope __device__ variable. On the host its name only
+// stands for the symbol; the device address is obtained once per device with
+// cudaGetSymbolAddress (on the first call that runs on that device, with that
+// device current) and passed to the kernel like any other pointer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "wg.h"
+#include "wg_internal.h"
+
+namespace wg {
+cudaError_t fused_launch(int cfg, const FusedArgs &args, int grid, int mode, cudaStream_t stream);
+cudaError_t fused_occupancy(int cfg, int *blocks);
+int fused_tile_points(int cfg);
+int fused_warps(int cfg);
+}  // namespace wg
+
+using namespace wg;
+
+namespace {
+
+// Layout of the fixed workspace: header | arrivals | per segment: count, max
+// y, merge scratch (4 ints + 4), staged hood coordinates (kStageCorners).
+constexpr int kNoAllocSegments = 2048;
+constexpr size_t kNaOffArrivals = 256;
+constexpr size_t kNaOffCount = 512;
+constexpr size_t kNaOffYmax = kNaOffCount + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaOffLive = kNaOffYmax + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaOffXy = kNaOffLive + 16 * (size_t)kNoAllocSegments + 16;
+constexpr size_t kNaBytes = kNaOffXy + 8 * (size_t)kStageCorners * kNoAllocSegments;  // about 2.2 MB
+// Bytes that every call must see as zero: the status word, the counters and
+// the arrival count of the last-segment merge.
+constexpr size_t kNaZeroBytes = kNaOffCount;
+constexpr int kNaTileCfg = 3;
+
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNaBytes];
+
+std::mutex g_na_mu;
+void *g_na_ptr[64] = {nullptr};
+
+inline cudaStream_t S(wg_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32_t *out_idx,
+                                           int32_t *out_count, wg_stream_t stream)
+{
+    if (n < 0) return WG_ERR_INVALID_VALUE;
+    if (n > INT32_MAX) return WG_ERR_UNSUPPORTED;
+    if (n > 0 && (!points || (reinterpret_cast<uintptr_t>(points) & 7u))) return WG_ERR_INVALID_VALUE;
+    if (!out_idx || !out_count || (reinterpret_cast<uintptr_t>(out_idx) & 3u) ||
+        (reinterpret_cast<uintptr_t>(out_count) & 3u))
+        return WG_ERR_INVALID_VALUE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WG_ERR_CUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return WG_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return WG_ERR_UNSUPPORTED;
+
+    // Set-up, once per device, with that device current.
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || !p) return WG_ERR_CUDA;
+            g_na_ptr[dev] = p;
+        }
+        ws = g_na_ptr[dev];
+    }
+
+    cudaStream_t s = S(stream);
+    if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+
+    // The array keeps the previous call's contents: clear the part that must
+    // start at zero.
+    if (cudaMemsetAsync(ws, 0, kNaZeroBytes, s) != cudaSuccess) return WG_ERR_CUDA;
+
+    int blocks = 0;
+    if (fused_occupancy(kNaTileCfg, &blocks) != cudaSuccess) return WG_ERR_CUDA;
+    const int T = fused_tile_points(kNaTileCfg);
+    const int W = fused_warps(kNaTileCfg);
+    const long long tiles = (n + T - 1) / T;
+    const long long warps = (long long)std::max(1, blocks) * prop.multiProcessorCount * W;
+    const long long nseg = std::min<long long>(std::min<long long>(tiles, warps), kNoAllocSegments);
+    const int grid = (int)((nseg + W - 1) / W);
+
+    char *w = static_cast<char *>(ws);
+    FusedArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.points = points;
+    a.out_idx = out_idx;
+    a.out_count = out_count;
+    a.n = n;
+    a.tiles = (int)tiles;
+    a.nseg = (int)nseg;
+    a.hdr = reinterpret_cast<WsHeader *>(w);
+    a.arrivals = reinterpret_cast<unsigned *>(w + kNaOffArrivals);
+    a.seg_count = reinterpret_cast<int *>(w + kNaOffCount);
+    a.seg_ymax = reinterpret_cast<float *>(w + kNaOffYmax);
+    a.seg_live = reinterpret_cast<int *>(w + kNaOffLive);
+    a.seg_xy = reinterpret_cast<float *>(w + kNaOffXy);
+    return fused_launch(kNaTileCfg, a, grid, 0, s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+}
