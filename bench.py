@@ -192,6 +192,28 @@ def run_reference(args, world, rank):
     """Reference arm: the CPU oracle timed as the step, on this workload."""
     if rank != 0:
         return
+    if args.workload == "batched":
+        from paper_1203_5004_gb300 import inputs
+        import oracle
+        S = args.sets
+        ps, offs, _ = inputs.batched(S, seed=5)
+        oracle.upper_hull(ps.kx[:1000], ps.ky[:1000])
+        t0 = time.perf_counter()
+        oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+        el = time.perf_counter() - t0
+        value = S / el
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": world,
+            "steps": 1, "warmup": 0, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"batched {S} sets, sizes log-uniform in [3, 65536], mixed kinds", "sets": S,
+                       "points": int(offs[-1]), "seed": 5},
+            "cpu_baseline": {"value": value, "unit": "sets/s", "cores": 1, "kind": "oracle",
+                             "sample": f"all {S} sets once, single-thread monotone chain"},
+            "e2e": {"value": value, "unit": "sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     kind, n, seed, desc = WORKLOADS[args.workload]
     ps = make_input(kind, n, seed)
     import oracle
@@ -216,6 +238,116 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+DEFAULT_COMPARE = {
+    "band26": ("counters", "fp64_only"),
+    "gauss28": ("plain",),
+}
+
+
+def time_steps(fn, steps, stream, dev):
+    """Average ms per call of fn over `steps` calls, CUDA events on `stream`."""
+    import torch
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / steps
+
+
+def run_batched(args, world, rank, local):
+    """Many sets in one launch vs one wg_upper_hood call per set."""
+    import ctypes
+
+    import torch
+    from paper_1203_5004_gb300 import _lib, inputs, wagener
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    S = args.sets
+    ps, offs, _ = inputs.batched(S, seed=rank_seed(5, rank))
+    total = int(offs[-1])
+    pts = torch.from_numpy(ps.points()).to(dev)
+    offs_d = torch.from_numpy(offs).to(dev)
+    out = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    counts = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    ws = wagener.new_workspace(wagener.batched_workspace_size(offs), dev)
+    stream = torch.cuda.current_stream(dev)
+    step = lambda: wagener.upper_hood_batched_into(pts, offs_d, out, counts, ws)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = args.steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    ms = time_steps(step, K, stream, dev)
+    clocks = sampler.stop()
+    ms = max_over_ranks(ms, pg, dev)
+    value = S * world / (ms * 1e-3)
+    hsum = int(counts.sum().item())
+
+    # The plain per-set form: one wg_upper_hood call per set, same GPU.
+    lib = _lib.load()
+    wsz = lib.wg_upper_hood_workspace_size(0)
+    pws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
+    pout = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    pcnt = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
+    base_p, base_o, base_c = pts.data_ptr(), pout.data_ptr(), pcnt.data_ptr()
+    sc = stream.cuda_stream
+    fn = lib.wg_upper_hood
+
+    def plain_sets():
+        for s_ in range(S):
+            a_, b_ = int(offs[s_]), int(offs[s_ + 1])
+            fn(base_p + 8 * a_, b_ - a_, base_o + 4 * a_, base_c + 4 * s_, pws.data_ptr(), wsz, sc)
+    plain_sets()
+    plain_ms = time_steps(plain_sets, 1, stream, dev)
+    same = bool(torch.equal(pcnt[:S], counts[:S]))
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    import oracle
+    t0 = time.perf_counter()
+    oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    cpu_s = time.perf_counter() - t0
+    peak, peak_kind = measured_peak()
+    alg = 8 * total + 4 * hsum + 8 * (S + 1) + 4 * S
+    line = {
+        "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched {S} sets, sizes log-uniform in [3, 65536], mixed kinds",
+                   "sets": S, "points": total, "corners": hsum, "seed": 5,
+                   "gpoints_per_s": total / (ms * 1e-3) / 1e9,
+                   "l2": "input > 129 MB L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "compare": {"plain_per_set_ms_per_step": plain_ms, "plain_per_set_sets_per_s": S / (plain_ms * 1e-3),
+                    "batched_speedup": plain_ms / ms, "plain_counts_equal": same},
+        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "fused_kernel (batched)", "alg_bytes_per_launch": alg},
+        "e2e": {"value": None, "unit": "sets/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "gpu_launches": 2 * K,
+        "clocks": clocks,
+        "cpu_baseline": {"value": S / cpu_s, "unit": "sets/s", "cores": 1, "kind": "oracle",
+                         "sample": f"all {S} sets once, single-thread monotone chain, {cpu_s:.1f} s"},
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1203_5004_gb300 import wagener
@@ -235,7 +367,12 @@ def run_ours(args, world, rank, local):
     ws = wagener.new_workspace(wagener.workspace_size(n), dev)
     stream = torch.cuda.current_stream(dev)
 
-    opts = wagener.autotune(pts, workspace=ws) if not args.no_autotune else wagener.default_options()
+    if args.tile_config:
+        opts = wagener.default_options(tile_config=args.tile_config)
+    elif args.no_autotune:
+        opts = wagener.default_options()
+    else:
+        opts = wagener.autotune(pts, workspace=ws)
     for _ in range(max(3, args.warmup)):
         wagener.upper_hood_into(pts, out, cnt, ws, opts)
     torch.cuda.synchronize(dev)
@@ -298,6 +435,45 @@ def run_ours(args, world, rank, local):
     e2e_s = max_over_ranks(e2e_s, pg, dev)
     e2e_value = n * world * e2e_steps / e2e_s / 1e9
 
+    # Other forms of the same step, untimed in `value` (reported in `compare`).
+    compare = {}
+    wants = set(args.compare.split(",")) if args.compare else set(DEFAULT_COMPARE.get(args.workload, ()))
+    if "counters" in wants:
+        co = wagener.default_options(tile_config=int(opts.tile_config), segments_per_cta=int(opts.segments_per_cta),
+                                     count_predicates=1)
+        wagener.read_counters(ws)
+        wagener.upper_hood_into(pts, out, cnt, ws, co)
+        tests, fb = wagener.read_counters(ws)
+        compare["orient_tests"] = tests
+        compare["fp64_fallbacks"] = fb
+        compare["filter_failure_rate"] = fb / tests if tests else 0.0
+    if "fp64_only" in wants:
+        fo = wagener.default_options(tile_config=int(opts.tile_config), segments_per_cta=int(opts.segments_per_cta),
+                                     pred_mode=1)
+        ref = out[:h].clone()
+        ms = time_steps(lambda: wagener.upper_hood_into(pts, out, cnt, ws, fo), min(K, 50), stream, dev)
+        compare["fp64_only_ms_per_step"] = ms
+        compare["fp64_only_gpoints_per_s"] = n / (ms * 1e-3) / 1e9
+        compare["fp64_only_same_output"] = bool(int(cnt.item()) == h and torch.equal(out[:h], ref))
+    if "plain" in wants:
+        pws = wagener.new_workspace(wagener.plain_workspace_size(n), dev)
+        pout = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        pcnt = torch.empty(1, dtype=torch.int32, device=dev)
+
+        def plain_step():
+            from paper_1203_5004_gb300 import _lib
+            import ctypes
+            _lib.check(_lib.load().wg_upper_hood_plain(pts.data_ptr(), n, pout.data_ptr(), pcnt.data_ptr(),
+                                                       pws.data_ptr(), pws.numel(), None, stream.cuda_stream),
+                       "wg_upper_hood_plain")
+        plain_step()
+        ms = time_steps(plain_step, min(K, 10), stream, dev)
+        compare["plain_ms_per_step"] = ms
+        compare["plain_gpoints_per_s"] = n / (ms * 1e-3) / 1e9
+        compare["plain_launches_per_step"] = max(1, (n - 1).bit_length())
+        compare["plain_same_output"] = bool(int(pcnt.item()) == h and torch.equal(pout[:h], out[:h]))
+        del pws
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -325,6 +501,8 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": {"value": cpu_gpts, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
                          "sample": f"full input, {reps} runs of the single-thread monotone chain, {el:.1f} s"},
     }
+    if compare:
+        line["compare"] = compare
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -336,14 +514,21 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS) + ["batched"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile-config", type=int, default=0, help="fixed tile configuration (0: autotune)")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and the K steps (for ncu); prints no bench line")
+    ap.add_argument("--compare", default="",
+                    help="comma list of extra forms to time: counters, fp64_only, plain")
+    ap.add_argument("--sets", type=int, default=100000, help="sets of the batched workload")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
         return
     run_ours(args, world, rank, local)
 

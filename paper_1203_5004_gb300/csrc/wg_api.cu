@@ -36,13 +36,13 @@ using namespace wg;
 namespace {
 
 // Single-set workspace: header | arrivals | per segment: count, max y,
-// final-merge scratch (4 ints), staged hood coordinates (kStageCorners).
+// final-merge scratch (16 ints), staged hood coordinates (kStageCorners).
 constexpr int kMaxSeg = 4096;        // segments (warp streams) of one fused call
 constexpr size_t kOffArrivals = 256;
 constexpr size_t kOffSegCount = 512;
 constexpr size_t kOffSegYmax = kOffSegCount + 4 * kMaxSeg;
 constexpr size_t kOffSegLive = kOffSegYmax + 4 * kMaxSeg;
-constexpr size_t kOffSegXy = kOffSegLive + 16 * kMaxSeg + 16;
+constexpr size_t kOffSegXy = kOffSegLive + 64 * kMaxSeg;
 constexpr size_t kSingleWsBytes = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
 constexpr int kDefaultCfg = 1;
 

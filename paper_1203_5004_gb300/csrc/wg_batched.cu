@@ -50,7 +50,7 @@ static BatchLayout batch_layout(int num_sets, long long max_items, long long max
     L.stage_xy = o;
     o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 8 * kStageCorners);
     L.stage_live = o;
-    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 16 + 16);
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 64);
     L.ctl = o;  // num_items, queue, done, bounds
     o = align256(o + 64);
     L.total = o;

@@ -61,7 +61,8 @@ struct Cfg {
     static constexpr size_t kOffDesc = kOffRidx + size_t(RCAP) * 4;
     static constexpr size_t kOffBar = kOffDesc + size_t(PCAP / 32) * 8;
     static constexpr size_t kWarpBytes = ((kOffBar + 8 * (S + 1)) + 127) / 128 * 128;
-    static constexpr size_t kBytes = kWarpBytes * W;
+    // after the warp regions: one CTA word (the item whose merge this CTA runs)
+    static constexpr size_t kBytes = kWarpBytes * W + 128;
     static_assert(K % 2 == 1 && K < 32, "K must be odd (bank-conflict-free strips) and < 32");
     static_assert(S >= 3, "three tile buffers: current, look-ahead, in flight");
     static_assert(RCAP % 64 == 0 && PCAP % 32 == 0 && PCAP >= 64, "window / list sizes");
@@ -94,7 +95,7 @@ struct SegStore {
     int *count;      // per slot: corners of the segment hood
     float *ymax;     // per slot: max y over the segment's points
     float2 *xy;      // per stage slot: coordinates of the hood (RCAP each), if it fit the window
-    int *live;       // per stage slot: scratch of the final merge (4 ints each)
+    int *live;       // per stage slot: scratch of the final merge (16 ints each)
 };
 
 template <class C, int MODE>
@@ -552,17 +553,26 @@ struct Warp {
             if (lane == 0) args.out_count[it.set] = count;
             return true;
         }
-        return publish_and_merge(it, item_index, R, pm_carry);
+        bool last = false;
+        publish(it, item_index, R, pm_carry, last);
+        if (last) {
+            if (args.items) {
+                // batched: the other warps are busy with other sets; merge alone
+                merge_set(it, item_index, 1, 0);
+            } else if (lane == 0) {
+                // single set: the whole CTA merges once its warps are done
+                *cta_flag() = item_index + 1;
+            }
+        }
+        return true;
     }
 
     // End of a segment of a multi-segment set: publish the segment hood (its
     // indices are already in the output array; its coordinates go to the
-    // workspace when it fits one window), its count and its max y. The warp
-    // that completes the set's last segment merges the segment hoods.
-    __device__ bool publish_and_merge(const SegItem &it, int item_index, RState &R, float segmax)
+    // workspace when it fits one window), its count and its max y. `last` is
+    // set in the warp that completed the set's last segment.
+    __device__ void publish(const SegItem &it, int item_index, RState &R, float segmax, bool &last)
     {
-        const float2 *P = reinterpret_cast<const float2 *>(args.points) + it.set_base;
-        int32_t *out = args.out_idx + it.set_base;
         const SegStore ss = store();
         const int count = R.g + R.w;
         const int stage0 = args.items ? args.items[item_index - it.c].pad : 0;
@@ -582,227 +592,271 @@ struct Warp {
             old = atomicAdd(args.arrivals + it.set, 1u);
         }
         old = __shfl_sync(kFull, old, 0);
-        if (old != (unsigned)(it.nseg - 1)) return true;
-        __threadfence();
-        const GlobSrc src{ss, out, P, args.items ? args.items + (item_index - it.c) : nullptr, it.slot0, stage0,
-                          (long long)args.tiles, args.nseg, it.nseg};
-        int *scratch = merge_scratch(it.nseg, ss.live + 4 * (size_t)stage0);
-        RState F{0, 0, out, P};
-        merge_hoods(src, scratch, F);
-        write_r(F);
-        if (lane == 0) {
-            args.out_count[it.set] = F.g + F.w;
-            args.arrivals[it.set] = 0;
-        }
-        __syncwarp();
-        return true;
+        last = old == (unsigned)(it.nseg - 1);
+        if (last) __threadfence();
     }
 
-    // ------------------------------------------------------- hood sources
-    // A merge pass takes a list of hoods, left to right, each with the max y
-    // over the points it came from, its corner count (negative, -count - 1,
-    // when its coordinates must be gathered through the indices) and its
-    // corners. fetch() loads a batch of up to 8 corners with all loads in
-    // flight at once.
-
-    // Hoods published in the workspace by other warps.
-    struct GlobSrc {
-        SegStore ss;
-        const int32_t *out;
+    // ------------------------------------------------------- final merge
+    // Corners of published segment hood c: staged coordinates when present,
+    // else gathered through the indices in the output array.
+    struct SegHood {
+        const float2 *xy;
+        const int32_t *idx;
         const float2 *P;
-        const SegItem *items;  // batched: the set's items; else nullptr
-        int slot0;             // count / max-y slot of entry 0
-        int stage0;            // stage slot of entry 0
-        long long tiles;       // single set: tiles and segments, to locate
-        int nseg;              //   segment starts
-        int n;                 // number of entries
-        __device__ float ymax(int i) const { return __ldcg(ss.ymax + slot0 + i); }
-        __device__ int rawcount(int i) const { return __ldcg(ss.count + slot0 + i); }
-        __device__ long long start(int i) const
-        {
-            if (items) return items[i].a;
-            return ((long long)i * tiles / nseg) * C::kT;
-        }
-        // corner `off` of hood c (raw count, start a) for each u with bit u set
-        __device__ __forceinline__ void fetch(unsigned valid, const int *c, const int *off, const int *raw,
-                                              const long long *a, float2 *p, int *id) const
-        {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if ((valid >> u) & 1u) id[u] = __ldcg(out + a[u] + off[u]);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (((valid >> u) & 1u) && raw[u] >= 0)
-                    p[u] = __ldcg(ss.xy + (size_t)(stage0 + c[u]) * C::kRCap + off[u]);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (((valid >> u) & 1u) && raw[u] < 0) p[u] = P[id[u]];
-        }
+        __device__ __forceinline__ float2 pt(int j) const { return xy ? __ldcg(xy + j) : P[__ldcg(idx + j)]; }
     };
 
-    // ------------------------------------------------------- merge pass
-    // Merge the hoods of src (left to right) into R. Hood staircase first: a
-    // hood is dropped whole when its max y is at most the max over all earlier
-    // hoods' points and below the max over some later hood's points (every
-    // corner of it then lies on or below a segment between two input points).
-    // The corners of the remaining hoods, concatenated in order, are streamed
-    // through the tile pass (no look-ahead). scratch: 4 * src.n + 1 ints.
-    template <class Src>
-    __device__ void merge_hoods(const Src &src, int *scratch, RState &R)
+    __device__ SegHood seg_hood(const SegStore &ss, const float2 *P, const int32_t *out, int stage0, int c,
+                                long long a_c, int raw) const
     {
-        const int nh = src.n;
-        float *yv = reinterpret_cast<float *>(scratch);
-        int *nv = scratch + nh;        // raw counts
-        int *live_seg = scratch + 2 * nh;
-        int *live_pre = scratch + 3 * nh;
-        // Metadata, with many loads in flight.
-        for (int c0 = 0; c0 < nh; c0 += 256) {
-            float y[8];
-            int r[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = c0 + u * 32 + lane;
-                if (c < nh) {
-                    y[u] = src.ymax(c);
-                    r[u] = src.rawcount(c);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = c0 + u * 32 + lane;
-                if (c < nh) {
-                    yv[c] = y[u];
-                    nv[c] = r[u];
-                }
-            }
-        }
-        __syncwarp();
-        // Backward sweep: max over later hoods (kept in live_pre for now).
-        float carry_suf = neg_inf();
-        for (int b0 = ((nh - 1) >> 5) << 5; b0 >= 0; b0 -= 32) {
-            const int c = b0 + lane;
-            const float ym = c < nh ? yv[c] : neg_inf();
-            const float isuf = warp_incl_suffix_max(ym);
-            float esuf = __shfl_down_sync(kFull, isuf, 1);
-            if (lane == 31) esuf = neg_inf();
-            if (c < nh) live_pre[c] = __float_as_int(fmaxf(esuf, carry_suf));
-            carry_suf = fmaxf(carry_suf, __shfl_sync(kFull, isuf, 0));
-        }
-        __syncwarp();
-        // Forward sweep: max over earlier hoods; keep the live hoods and the
-        // prefix of their corner counts.
-        float carry_pre = neg_inf();
-        int nlive = 0, total = 0;
-        for (int b0 = 0; b0 < nh; b0 += 32) {
-            const int c = b0 + lane;
-            float ym = neg_inf(), later = neg_inf();
-            int cntc = 0;
-            if (c < nh) {
-                ym = yv[c];
-                later = __int_as_float(live_pre[c]);
-                const int r = nv[c];
-                cntc = r < 0 ? -r - 1 : r;
-            }
-            const float ipre = warp_incl_prefix_max(ym);
-            float epre = __shfl_up_sync(kFull, ipre, 1);
-            if (lane == 0) epre = neg_inf();
-            const float before = fmaxf(epre, carry_pre);
-            const bool keep = c < nh && cntc > 0 && !(!(ym > before) && ym < later);
-            const unsigned km = __ballot_sync(kFull, keep);
-            const int kr = __popc(km & ((1u << lane) - 1u));
-            const int kc = keep ? cntc : 0;
-            const int incl = warp_incl_sum(kc);
-            __syncwarp();
-            if (keep) {
-                live_seg[nlive + kr] = c;
-                live_pre[nlive + kr] = total + incl - kc;
-            }
-            __syncwarp();
-            nlive += __popc(km);
-            total += __shfl_sync(kFull, incl, 31);
-            carry_pre = fmaxf(carry_pre, __shfl_sync(kFull, ipre, 31));
-        }
-        if (lane == 0) live_pre[nlive] = total;
-        __syncwarp();
+        SegHood h;
+        h.xy = raw >= 0 ? ss.xy + (size_t)(stage0 + c) * C::kRCap : nullptr;
+        h.idx = out + a_c;
+        h.P = P;
+        return h;
+    }
 
-        pn = 0;
-        float pm_carry = neg_inf();
-        float2 prev_pt = make_float2(0.f, 0.f);
-        bool has_prev = false;
-        float2 *t0 = buf(0);
-        int *ti = reinterpret_cast<int *>(buf(1));
-        int cur = 0;  // live hood holding the first entry of the tile
-        for (int v0 = 0; v0 < total; v0 += C::kT) {
-            const int cnt = total - v0 < C::kT ? total - v0 : C::kT;
-            // Each lane gathers its strip of K consecutive entries, walking
-            // forward through the live hoods, 8 corners per batch of loads.
-            const int e0 = lane * C::kK;
-            int l = cur;
-            if (e0 < cnt)
-                while (l + 1 < nlive && live_pre[l + 1] <= v0 + e0) ++l;
-            for (int jb = 0; jb < C::kK; jb += 8) {
-                int cc[8], off[8], raw[8];
-                long long aa[8];
-                float2 p[8];
-                int id[8];
-                unsigned valid = 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = e0 + jb + u;
-                    cc[u] = 0;
-                    off[u] = 0;
-                    raw[u] = 0;
-                    aa[u] = 0;
-                    p[u] = make_float2(0.f, 0.f);
-                    id[u] = 0;
-                    if (jb + u < C::kK && e < cnt) {
-                        const int v = v0 + e;
-                        while (live_pre[l + 1] <= v) ++l;
-                        cc[u] = live_seg[l];
-                        off[u] = v - live_pre[l];
-                        raw[u] = nv[cc[u]];
-                        aa[u] = src.start(cc[u]);
-                        valid |= 1u << u;
+    __device__ long long seg_start(const SegItem &it, int item_index, int c) const
+    {
+        if (args.items) return args.items[item_index - it.c + c].a;
+        return ((long long)c * args.tiles / args.nseg) * C::kT;
+    }
+
+    // Merge the published segment hoods of a set into its output, with nw
+    // warps (this one is number gw; nw == 1: this warp alone, else the whole
+    // CTA). Stages of the paper over the whole list at once:
+    //  1. hood staircase: a segment is dropped whole when its max y is at most
+    //     the max over all earlier segments and below the max over some later
+    //     one (its points then lie on or below a segment between two input
+    //     points);
+    //  2. the bridge (bridge_warp) of every adjacent pair of remaining hoods,
+    //     the pairs spread over the warps;
+    //  3. hood i keeps its corners from the left bridge's corner s_i to the
+    //     right bridge's corner e_i. If s_i > e_i, or s_i == e_i and that
+    //     corner is not a strict right turn between the two bridges, every
+    //     corner of hood i lies on or below the segment joining its
+    //     neighbours' bridge corners: hood i is dropped and the new adjacent
+    //     pairs are bridged; repeat until nothing is dropped;
+    //  4. the kept ranges are compacted into the output (mam 6).
+    // The resulting chain is strictly convex, runs from the first point to the
+    // last and has every input point on or below it: it is the upper hood.
+    __device__ __noinline__ void merge_set(const SegItem &it, int item_index, int nw, int gw)
+    {
+        const float2 *P = reinterpret_cast<const float2 *>(args.points) + it.set_base;
+        int32_t *out = args.out_idx + it.set_base;
+        const SegStore ss = store();
+        const int nh = it.nseg;
+        const int stage0 = args.items ? args.items[item_index - it.c].pad : 0;
+        const int slot0 = it.slot0;
+        const bool cta = nw > 1;
+        const int nthreads = nw * 32, t = gw * 32 + lane;
+        auto sync = [&]() {
+            if (cta) __syncthreads(); else __syncwarp();
+        };
+        // scratch: 12 nh + 8 ints
+        int *sm;
+        const size_t need = (size_t)(12 * nh + 8) * 4;
+        if (cta && need <= C::kWarpBytes * C::kW) sm = reinterpret_cast<int *>(base - C::kWarpBytes * (threadIdx.x >> 5));
+        else if (!cta && need <= (size_t)(C::kS - 2) * C::kBuf * 8) sm = reinterpret_cast<int *>(buf(2));
+        else sm = ss.live + (size_t)stage0 * 16;  // 16 ints per segment, >= 12 nh + 8 for nh >= 2
+        float *yv = reinterpret_cast<float *>(sm);
+        int *rv = sm + nh;
+        int *lidA = sm + 2 * nh, *bpA = sm + 3 * nh, *bqA = sm + 4 * nh, *pvA = sm + 5 * nh;
+        int *lidB = sm + 6 * nh, *bpB = sm + 7 * nh, *bqB = sm + 8 * nh, *pvB = sm + 9 * nh;
+        int *dead = sm + 10 * nh;
+        int *pos = sm + 11 * nh;  // nh + 1
+        int *ctl = sm + 12 * nh + 1;  // [0] = live count, [1] = any dropped
+
+        // 0. metadata
+        for (int c = t; c < nh; c += nthreads) {
+            yv[c] = __ldcg(ss.ymax + slot0 + c);
+            rv[c] = __ldcg(ss.count + slot0 + c);
+        }
+        sync();
+        // 1. hood staircase (first warp): lane-contiguous blocks
+        if (gw == 0) {
+            const int nb = (nh + 31) >> 5;
+            const int c0 = min(nh, lane * nb), c1 = min(nh, c0 + nb);
+            float bm = neg_inf();
+            for (int c = c0; c < c1; ++c) bm = fmaxf(bm, yv[c]);
+            const float ipre = warp_incl_prefix_max(bm);
+            const float isuf = warp_incl_suffix_max(bm);
+            float before = __shfl_up_sync(kFull, ipre, 1);
+            float later = __shfl_down_sync(kFull, isuf, 1);
+            if (lane == 0) before = neg_inf();
+            if (lane == 31) later = neg_inf();
+            // later maxima, right to left, kept in dead[] for now
+            for (int c = c1 - 1; c >= c0; --c) {
+                dead[c] = __float_as_int(later);
+                later = fmaxf(later, yv[c]);
+            }
+            int nk = 0;
+            for (int c = c0; c < c1; ++c) {
+                const float ym = yv[c];
+                const int r = rv[c];
+                const int cn = r < 0 ? -r - 1 : r;
+                const bool keep = cn > 0 && !(!(ym > before) && ym < __int_as_float(dead[c]));
+                pos[c] = keep;
+                nk += keep;
+                before = fmaxf(before, ym);
+            }
+            const int incl = warp_incl_sum(nk);
+            int k = incl - nk;
+            for (int c = c0; c < c1; ++c)
+                if (pos[c]) {
+                    lidA[k] = c;
+                    pvA[k] = 0;
+                    ++k;
+                }
+            if (lane == 31) ctl[0] = incl;
+        }
+        sync();
+        int nl = ctl[0];
+        int *lid = lidA, *bp = bpA, *bq = bqA, *pv = pvA;
+        int *lid2 = lidB, *bp2 = bpB, *bq2 = bqB, *pv2 = pvB;
+
+        // 2-3. bridges of adjacent hoods; drop the hoods that contribute nothing
+        for (int round = 0; round < nh + 1; ++round) {
+            for (int i = gw; i < nl - 1; i += nw) {
+                if (pv[i]) continue;
+                const int c = lid[i], d = lid[i + 1];
+                const int rc = rv[c], rd = rv[d];
+                const int hc = rc < 0 ? -rc - 1 : rc, hd = rd < 0 ? -rd - 1 : rd;
+                const SegHood A = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rc);
+                const SegHood B = seg_hood(ss, P, out, stage0, d, seg_start(it, item_index, d), rd);
+                const int2 pq = bridge_warp<MODE>(pc, A, hc, B, hd);
+                if (lane == 0) {
+                    bp[i] = pq.x;
+                    bq[i] = pq.y;
+                    pv[i] = 1;
+                }
+                __syncwarp();
+            }
+            sync();
+            int drop = 0;
+            for (int i = t; i < nl; i += nthreads) {
+                int dd = 0;
+                if (i > 0 && i < nl - 1) {
+                    const int si = bq[i - 1], ei = bp[i];
+                    if (si > ei) {
+                        dd = 1;
+                    } else if (si == ei) {
+                        const int c = lid[i], l = lid[i - 1], r = lid[i + 1];
+                        const float2 A = seg_hood(ss, P, out, stage0, l, seg_start(it, item_index, l), rv[l]).pt(bp[i - 1]);
+                        const float2 B = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rv[c]).pt(si);
+                        const float2 Cc = seg_hood(ss, P, out, stage0, r, seg_start(it, item_index, r), rv[r]).pt(bq[i]);
+                        dd = orient<MODE>(pc, A, B, Cc) >= 0;
                     }
                 }
-                if (__any_sync(kFull, valid != 0)) {
-                    src.fetch(valid, cc, off, raw, aa, p, id);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if ((valid >> u) & 1u) {
-                            t0[e0 + jb + u] = p[u];
-                            ti[e0 + jb + u] = id[u];
+                dead[i] = dd;
+                drop |= dd;
+            }
+            const bool any = cta ? __syncthreads_or(drop) : __any_sync(kFull, drop);
+            if (!any) break;
+            // compaction of the live list; a pair's bridge stays valid when
+            // its two hoods were already adjacent
+            if (gw == 0) {
+                int k = 0;
+                int prev_old = -2;
+                for (int b0 = 0; b0 < nl; b0 += 32) {
+                    const int i = b0 + lane;
+                    const bool alive = i < nl && !dead[i];
+                    const unsigned am = __ballot_sync(kFull, alive);
+                    const int r = __popc(am & ((1u << lane) - 1u));
+                    // old index of the alive hood just before me
+                    const int hi_prev = 31 - __clz(am & ((1u << lane) - 1u));
+                    int prev = hi_prev >= 0 ? b0 + hi_prev : prev_old;
+                    if (alive) {
+                        lid2[k + r] = lid[i];
+                        // pair (k + r - 1, k + r) valid iff the previous alive hood is i - 1
+                        if (k + r > 0) {
+                            const bool ok = prev == i - 1 && pv[i - 1];
+                            pv2[k + r - 1] = ok ? 1 : 0;
+                            if (ok) {
+                                bp2[k + r - 1] = bp[i - 1];
+                                bq2[k + r - 1] = bq[i - 1];
+                            }
                         }
+                    }
+                    if (am) prev_old = b0 + 31 - __clz(am);
+                    k += __popc(am);
+                    __syncwarp();
+                }
+                if (lane == 0) ctl[0] = k;
+            }
+            sync();
+            nl = ctl[0];
+            int *tmp;
+            tmp = lid; lid = lid2; lid2 = tmp;
+            tmp = bp; bp = bp2; bp2 = tmp;
+            tmp = bq; bq = bq2; bq2 = tmp;
+            tmp = pv; pv = pv2; pv2 = tmp;
+            sync();
+        }
+
+        // 4. output: ranges [s_i, e_i] of the kept hoods, packed in order.
+        if (gw == 0) {
+            const int nb = (nl + 31) >> 5;
+            const int i0 = min(nl, lane * nb), i1 = min(nl, i0 + nb);
+            int sum = 0;
+            for (int i = i0; i < i1; ++i) {
+                const int r = rv[lid[i]];
+                const int hi = r < 0 ? -r - 1 : r;
+                const int si = i > 0 ? bq[i - 1] : 0, ei = i < nl - 1 ? bp[i] : hi - 1;
+                sum += ei - si + 1;
+            }
+            const int incl = warp_incl_sum(sum);
+            int run = incl - sum;
+            for (int i = i0; i < i1; ++i) {
+                pos[i] = run;
+                const int r = rv[lid[i]];
+                const int hi = r < 0 ? -r - 1 : r;
+                const int si = i > 0 ? bq[i - 1] : 0, ei = i < nl - 1 ? bp[i] : hi - 1;
+                run += ei - si + 1;
+            }
+            if (lane == 31) pos[nl] = incl;
+        }
+        sync();
+        // Copy in batches [i0, i1) whose destinations all lie below every
+        // source in the batch (destinations never exceed sources); batches run
+        // one after the other.
+        int i0 = 0;
+        while (i0 < nl) {
+            const long long a0 = seg_start(it, item_index, lid[i0]) + (i0 > 0 ? bq[i0 - 1] : 0);
+            int i1 = i0 + 1;
+            while (i1 < nl && (long long)pos[i1 + 1] <= a0) ++i1;
+            for (int i = i0 + gw; i < i1; i += nw) {
+                const int c = lid[i];
+                const long long ac = seg_start(it, item_index, c);
+                const int r = rv[c];
+                const int hi = r < 0 ? -r - 1 : r;
+                const int si = i > 0 ? bq[i - 1] : 0, ei = i < nl - 1 ? bp[i] : hi - 1;
+                const int len = ei - si + 1, dst = pos[i];
+                if ((long long)dst == ac + si) continue;  // already in place
+                for (int b0 = 0; b0 < len; b0 += 32) {
+                    const int k = b0 + lane;
+                    int v = 0;
+                    if (k < len) v = __ldcg(out + ac + si + k);
+                    __syncwarp();
+                    if (k < len) out[dst + k] = v;
+                    __syncwarp();
                 }
             }
-            while (cur + 1 < nlive && live_pre[cur + 1] <= v0 + C::kT) ++cur;
-            __syncwarp();
-            const float ym = strip_max(t0, cnt);
-            decide<true>(t0, cnt, 0, ti, ym, neg_inf(), pm_carry, prev_pt, has_prev, R);
-            __syncwarp();
+            __threadfence_block();
+            sync();
+            i0 = i1;
         }
-        flush_pending(R);
+        if (t == 0) {
+            args.out_count[it.set] = pos[nl];
+            args.arrivals[it.set] = 0;
+        }
+        sync();
     }
 
-    // Scratch for a merge pass over nh hoods (4 nh + 1 ints). Single set: the
-    // merging warp completed the last segment, so every other warp of its CTA
-    // has finished with its shared memory; use the larger run of their
-    // regions. Batched: this warp's free tile buffers, else the workspace.
-    __device__ int *merge_scratch(int nh, int *global_scratch) const
+    __device__ int *cta_flag() const
     {
-        const size_t need = (size_t)(4 * nh + 1) * 4;
-        if (!args.items) {
-            const int w = threadIdx.x >> 5;
-            unsigned char *cta = base - C::kWarpBytes * w;
-            const int after = C::kW - 1 - w;
-            if (after >= w && (size_t)after * C::kWarpBytes >= need)
-                return reinterpret_cast<int *>(cta + C::kWarpBytes * (w + 1));
-            if (w > after && (size_t)w * C::kWarpBytes >= need) return reinterpret_cast<int *>(cta);
-        }
-        if (need <= (size_t)(C::kS - 2) * C::kBuf * 8) return reinterpret_cast<int *>(buf(2));
-        return global_scratch;
+        return reinterpret_cast<int *>(base - C::kWarpBytes * (threadIdx.x >> 5) + C::kWarpBytes * C::kW);
     }
-
 };
 
 template <class C, int MODE>
@@ -816,7 +870,8 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
         for (int s = 0; s <= C::kS; ++s) mbar_init(bars + s, 1);
         fence_mbar_init();
     }
-    __syncwarp();
+    if (threadIdx.x == 0) *Wk.cta_flag() = 0;
+    __syncthreads();
 
     // Test hook: one bounded wait on a barrier that nothing completes.
     const int stall = args.hdr->stall_test_ns;
@@ -854,6 +909,15 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
         const int gw = blockIdx.x * C::kW + warp, nw = gridDim.x * C::kW;
         for (int i = gw; i < nitems; i += nw)
             if (!Wk.run_segment(i, seq)) break;
+        // The CTA whose warp completed the set's last segment merges the
+        // segment hoods with all its warps (every other warp is done).
+        __syncthreads();
+        const int flag = *Wk.cta_flag();
+        if (flag) {
+            __threadfence();
+            const SegItem it = Wk.item(flag - 1);
+            Wk.merge_set(it, flag - 1, C::kW, warp);
+        }
     }
 
     if (MODE & kModeCount) {

@@ -48,7 +48,7 @@ struct FusedArgs {
     int *seg_count;          // one per segment slot (negative: coordinates not staged)
     float *seg_ymax;         // one per segment slot: max y of the segment
     float *seg_xy;           // per stage slot: kStageCorners float2 (segment hood coordinates)
-    int *seg_live;           // per stage slot: 4 ints of final-merge scratch (+1)
+    int *seg_live;           // per stage slot: 16 ints of final-merge scratch
     unsigned *arrivals;      // one per set
 };
 

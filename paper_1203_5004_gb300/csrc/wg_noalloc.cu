@@ -37,13 +37,13 @@ using namespace wg;
 namespace {
 
 // Layout of the fixed workspace: header | arrivals | per segment: count, max
-// y, merge scratch (4 ints + 4), staged hood coordinates (kStageCorners).
+// y, merge scratch (16 ints), staged hood coordinates (kStageCorners).
 constexpr int kNoAllocSegments = 2048;
 constexpr size_t kNaOffArrivals = 256;
 constexpr size_t kNaOffCount = 512;
 constexpr size_t kNaOffYmax = kNaOffCount + 4 * (size_t)kNoAllocSegments;
 constexpr size_t kNaOffLive = kNaOffYmax + 4 * (size_t)kNoAllocSegments;
-constexpr size_t kNaOffXy = kNaOffLive + 16 * (size_t)kNoAllocSegments + 16;
+constexpr size_t kNaOffXy = kNaOffLive + 64 * (size_t)kNoAllocSegments;
 constexpr size_t kNaBytes = kNaOffXy + 8 * (size_t)kStageCorners * kNoAllocSegments;  // about 2.2 MB
 // Bytes that every call must see as zero: the status word, the counters and
 // the arrival count of the last-segment merge.

@@ -275,6 +275,23 @@ def test_batched(wg, num_sets, hi):
         assert_same(out[a:a + cnt[s]], ref_out[a:a + ref_cnt[s]], f"set {s}")
 
 
+@pytest.mark.slow
+def test_batched_full_100k(wg):
+    # the batched workload at its full size (100,000 sets), every set checked
+    ps, offs, _ = inputs.batched(100_000, seed=5)
+    ref_out, ref_cnt = oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    out, cnt = wg.upper_hood_batched(gpu_points(ps), offs)
+    out, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+    assert_same(cnt, ref_cnt, "batched counts")
+    # corners: compare the CSR-aligned arrays on every set's valid prefix at once
+    n = offs[-1]
+    valid = np.zeros(n, dtype=bool)
+    starts = offs[:-1]
+    for s in np.nonzero(ref_cnt)[0]:
+        valid[starts[s]:starts[s] + ref_cnt[s]] = True
+    assert np.array_equal(out[:n][valid], ref_out[:n][valid])
+
+
 def test_batched_with_empty_and_large_sets(wg):
     sizes = [0, 1, 2, 0, 5, 300_000, 0, 7, 1_000_000, 3]
     sets = [inputs.make(k, n, i) for i, (k, n) in enumerate(zip(
