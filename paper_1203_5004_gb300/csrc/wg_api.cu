@@ -36,14 +36,18 @@ using namespace wg;
 namespace {
 
 // Single-set workspace: header | arrivals | per segment: count, max y,
-// final-merge scratch (16 ints), staged hood coordinates (kStageCorners).
+// final-merge scratch (16 ints), staged hood coordinates and indices
+// (kStageCorners), pair word and pair bridge.
 constexpr int kMaxSeg = 4096;        // segments (warp streams) of one fused call
 constexpr size_t kOffArrivals = 256;
 constexpr size_t kOffSegCount = 512;
 constexpr size_t kOffSegYmax = kOffSegCount + 4 * kMaxSeg;
 constexpr size_t kOffSegLive = kOffSegYmax + 4 * kMaxSeg;
 constexpr size_t kOffSegXy = kOffSegLive + 64 * kMaxSeg;
-constexpr size_t kSingleWsBytes = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
+constexpr size_t kOffSegSidx = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
+constexpr size_t kOffSegPair = kOffSegSidx + 4 * (size_t)kStageCorners * kMaxSeg;
+constexpr size_t kOffSegBridge = kOffSegPair + 4 * (size_t)kMaxSeg;
+constexpr size_t kSingleWsBytes = kOffSegBridge + 8 * (size_t)kMaxSeg;
 constexpr int kDefaultCfg = 1;
 
 struct DevInfo {
@@ -212,6 +216,9 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     a.seg_ymax = reinterpret_cast<float *>(static_cast<char *>(workspace) + kOffSegYmax);
     a.seg_live = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffSegLive);
     a.seg_xy = reinterpret_cast<float *>(static_cast<char *>(workspace) + kOffSegXy);
+    a.seg_sidx = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffSegSidx);
+    a.seg_pair = reinterpret_cast<unsigned *>(static_cast<char *>(workspace) + kOffSegPair);
+    a.seg_bridge = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + kOffSegBridge);
     if (fused_launch(cfg, a, grid, pred_mode_bits(o), S(stream)) != cudaSuccess) return WG_ERR_CUDA;
     return WG_OK;
 }

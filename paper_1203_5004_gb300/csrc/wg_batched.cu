@@ -26,7 +26,7 @@ constexpr int kPlanThreads = 1024;
 constexpr int kBins = 3;
 
 struct BatchLayout {
-    size_t arrivals, seg_count, seg_ymax, items, stage_xy, stage_live, ctl, total;
+    size_t arrivals, seg_count, seg_ymax, items, stage_xy, stage_sidx, stage_live, stage_pair, stage_bridge, ctl, total;
     long long max_items, max_stage;
 };
 
@@ -49,8 +49,14 @@ static BatchLayout batch_layout(int num_sets, long long max_items, long long max
     o = align256(o + (size_t)std::max<long long>(max_items, 1) * sizeof(SegItem));
     L.stage_xy = o;
     o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 8 * kStageCorners);
+    L.stage_sidx = o;
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 4 * kStageCorners);
     L.stage_live = o;
     o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 64);
+    L.stage_pair = o;
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 4);
+    L.stage_bridge = o;
+    o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 8);
     L.ctl = o;  // num_items, queue, done, bounds
     o = align256(o + 64);
     L.total = o;
@@ -196,6 +202,9 @@ cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_
     a.seg_ymax = reinterpret_cast<float *>(w + L.seg_ymax);
     a.seg_xy = reinterpret_cast<float *>(w + L.stage_xy);
     a.seg_live = reinterpret_cast<int *>(w + L.stage_live);
+    a.seg_sidx = reinterpret_cast<int *>(w + L.stage_sidx);
+    a.seg_pair = reinterpret_cast<unsigned *>(w + L.stage_pair);
+    a.seg_bridge = reinterpret_cast<unsigned long long *>(w + L.stage_bridge);
     a.arrivals = reinterpret_cast<unsigned *>(w + L.arrivals);
     const int grid = std::max(1, blocks) * sms;
     return fused_launch(cfg, a, grid, mode, st);

@@ -44,8 +44,93 @@
 namespace wg {
 
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s bound on any device wait
-
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+constexpr int kShearLanes = 3;  // more surviving strips than this: shear the tile
+
+// The frame in which a tile's points are compared by height: y itself, or
+// the sheared y' = (y - y0) - s (x - x0). Shearing keeps every orientation.
+// x - x0 and y - y0 are exact for points on the grid; the two other roundings
+// are bounded per point, so lo = y' - e <= exact y' <= hi = y' + e with
+// e = 2^-22 (|s (x - x0)| + |y'|). With s = 0 all of it is exact and e = 0.
+struct Frame {
+    float x0, y0, s, ec;
+    __device__ __forceinline__ void bounds(float2 v, float &lo, float &hi) const
+    {
+        const float t = __fmul_rn(s, __fsub_rn(v.x, x0));
+        const float yp = __fsub_rn(__fsub_rn(v.y, y0), t);
+        const float e = __fmul_rn(__fadd_rn(fabsf(t), fabsf(yp)), ec);
+        lo = __fsub_rn(yp, e);
+        hi = __fadd_rn(yp, e);
+    }
+};
+
+// A tile decided in the frame sheared by its chord slope (from its first to
+// its last point), for tiles where the plain height test leaves many strips:
+// points along a sloped curve. Heights are intervals (see Frame): a strip goes
+// when the lows before it reach its high and a low after it exceeds its high;
+// inside a strip each point is tested the same way. The frame is kept only if
+// fewer strips survive than the plain test's `live_plain`. Returns the lane's
+// mask of remaining points in the low 32 bits and 1 in bit 32 when the frame
+// is kept (warp-uniform), 0 otherwise. Not inlined: it runs on few tiles and
+// stays out of the hot loop's code.
+template <int K>
+__device__ __noinline__ unsigned long long sheared_tile(const float2 *tb, int cnt, int nvalid, int live_plain,
+                                                       float2 prev_pt, bool has_prev)
+{
+    const int lane = threadIdx.x & 31;
+    const int sbase = lane * K;
+    const float2 f0 = tb[0], f1 = tb[cnt - 1];
+    float sl = f1.x > f0.x ? (f1.y - f0.y) / (f1.x - f0.x) : 0.f;
+    if (!(fabsf(sl) < 1e6f)) sl = 0.f;
+    const Frame f{f0.x, f0.y, sl, sl != 0.f ? 0x1p-22f : 0.f};
+    const int m = min(K, nvalid);
+    float mlo = neg_inf(), mhi = neg_inf();
+#pragma unroll 1
+    for (int j = 0; j < m; ++j) {
+        float l, h;
+        f.bounds(tb[sbase + j], l, h);
+        mlo = fmaxf(mlo, l);
+        mhi = fmaxf(mhi, h);
+    }
+    float carry = neg_inf();
+    if (has_prev) {
+        float h;
+        f.bounds(prev_pt, carry, h);
+    }
+    const float jpre = warp_incl_prefix_max(mlo);
+    const float jsuf = warp_incl_suffix_max(mlo);
+    float pre = __shfl_up_sync(kFull, jpre, 1);
+    float suf = __shfl_down_sync(kFull, jsuf, 1);
+    if (lane == 0) pre = neg_inf();
+    if (lane == 31) suf = neg_inf();
+    const float pm0 = fmaxf(carry, pre);
+    const bool dead = !(mhi > pm0) && mhi < suf;
+    const unsigned live = __ballot_sync(kFull, !dead && nvalid > 0);
+    if (__popc(live) >= live_plain) return 0ull;
+    unsigned surv = 0;
+    if (!dead && nvalid > 0) {
+        unsigned kpre = 0;
+        float pm = pm0;
+#pragma unroll 1
+        for (int j = 0; j < m; ++j) {
+            float lo, hi;
+            f.bounds(tb[sbase + j], lo, hi);
+            kpre |= (hi <= pm ? 1u : 0u) << j;
+            pm = fmaxf(pm, lo);
+        }
+        float smx = suf;
+#pragma unroll 1
+        for (int j = m - 1; j >= 0; --j) {
+            float lo, hi;
+            f.bounds(tb[sbase + j], lo, hi);
+            if (!(((kpre >> j) & 1u) && hi < smx)) surv |= 1u << j;
+            smx = fmaxf(smx, lo);
+        }
+    }
+    return (1ull << 32) | surv;
+}
+
 
 template <int W, int K, int S, int RCAP, int PCAP>
 struct Cfg {
@@ -95,8 +180,15 @@ struct SegStore {
     int *count;      // per slot: corners of the segment hood
     float *ymax;     // per slot: max y over the segment's points
     float2 *xy;      // per stage slot: coordinates of the hood (RCAP each), if it fit the window
+    int *sidx;       // per stage slot: indices of the hood (RCAP each), staged with xy
     int *live;       // per stage slot: scratch of the final merge (16 ints each)
+    unsigned *pair;  // per stage slot: publication tag of the pair (this, next)
+    unsigned long long *bridge;  // per stage slot: bridge of the pair (this, next), tagged
 };
+
+// Tags of one call: the workspace's call counter + 1, mixed with a constant
+// so that no other word of any workspace layout can equal a tag.
+constexpr unsigned kTagMix = 0x9E3779B9u;
 
 template <class C, int MODE>
 struct Warp {
@@ -105,6 +197,10 @@ struct Warp {
     PredCount pc;
     int lane;
     int pn;               // corners in the pending list
+    float xfirst;         // x of the set's first point (column rule)
+    int sh_skip, sh_fail;  // sheared-frame trials: tiles to skip, failures in a row
+    unsigned tag;          // this call's tag (pair words, pair bridges)
+    int pp_item, pp_count; // single set: the segment whose pair bridges wait for the CTA (-1: none)
 
     __device__ Warp(const FusedArgs &a, unsigned char *b) : args(a), base(b), pn(0) { lane = threadIdx.x & 31; }
 
@@ -141,7 +237,10 @@ struct Warp {
         s.count = args.seg_count;
         s.ymax = args.seg_ymax;
         s.xy = reinterpret_cast<float2 *>(args.seg_xy);
+        s.sidx = args.seg_sidx;
         s.live = args.seg_live;
+        s.pair = args.seg_pair;
+        s.bridge = args.seg_bridge;
         return s;
     }
 
@@ -316,11 +415,12 @@ struct Warp {
         __syncwarp();
     }
 
-    // Survivors of one strip (not all dropped): per-point elimination, first
-    // occurrence, then the strip's hood by a monotone scan whose stack is a bit
-    // mask (top two corners in registers, deeper ones re-read).
-    __device__ __forceinline__ unsigned strip_corners(const float2 *tb, int sbase, int nvalid, float pm0,
-                                                   float sm0, float2 prev_pt, bool has_prev)
+    // Per-point elimination in one strip (not all dropped), by height: a
+    // point goes when everything before it reaches its height and something
+    // after it is strictly higher. pm0 / sm0: max height before / after the
+    // strip. Returns the mask of the strip's points that remain.
+    __device__ __forceinline__ unsigned elim_plain(const float2 *tb, int sbase, int nvalid, float pm0,
+                                                   float sm0) const
     {
         constexpr int K = C::kK;
         float py[K];
@@ -340,7 +440,16 @@ struct Warp {
             if (!(((kpre >> j) & 1u) && py[j] < smx)) surv |= 1u << j;
             smx = fmaxf(smx, py[j]);
         }
-        surv &= nvalid >= K ? ((1u << K) - 1u) : ((1u << nvalid) - 1u);
+        return surv & (nvalid >= K ? ((1u << K) - 1u) : ((1u << nvalid) - 1u));
+    }
+
+    // The strip's corners among the points that remain (surv): first
+    // occurrence, the column rule, then the strip's hood by a monotone scan
+    // whose stack is a bit mask (top two corners in registers, deeper ones
+    // re-read).
+    __device__ __forceinline__ unsigned strip_corners(const float2 *tb, int sbase, int nvalid, unsigned surv,
+                                                      float2 prev_pt, bool has_prev)
+    {
         unsigned hm = 0;
         int hn = 0;
         float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
@@ -355,6 +464,14 @@ struct Warp {
                 hv = true;
             }
             if (hv && same_point(pv, Pj)) continue;  // a repeat: first occurrence wins
+            // Column rule: a point with a strictly higher point directly above
+            // it is not a corner when the point below it is in the same column
+            // (three collinear points) or some point lies further left (it is
+            // then strictly below the segment from the set's first point).
+            if (j + 1 < nvalid) {
+                const float2 nx = tb[sbase + j + 1];
+                if (nx.x == Pj.x && nx.y > Pj.y && ((hv && pv.x == Pj.x) || Pj.x > xfirst)) continue;
+            }
             while (hn >= 2 && orient<MODE>(pc, A, B, Pj) >= 0) {
                 hm &= ~(1u << (31 - __clz(hm)));
                 --hn;
@@ -438,7 +555,26 @@ struct Warp {
         // Whole strip dropped: everything before it is at least as high as its
         // maximum, and something after it is strictly higher.
         const bool dead = !(ymax_mine > pm0) && ymax_mine < sm0;
-        if (!dead && nvalid > 0) hm = strip_corners(tb, sbase, nvalid, pm0, sm0, prev_pt, has_prev);
+        const unsigned live = __ballot_sync(kFull, !dead && nvalid > 0);
+        unsigned surv = 0;
+        bool sheared = false;
+        if (sh_skip > 0) {
+            --sh_skip;
+        } else if (__popc(live) > kShearLanes) {
+            // Many strips survive: try the sheared frame. After a trial that
+            // does not pay, skip the next 2, 4, ... 64 tiles' trials.
+            const unsigned long long r = sheared_tile<K>(tb, cnt, nvalid, __popc(live), prev_pt, has_prev);
+            if (r >> 32) {
+                sheared = true;
+                surv = (unsigned)r;
+                sh_fail = 0;
+            } else {
+                sh_fail = min(sh_fail + 1, 6);
+                sh_skip = 1 << sh_fail;
+            }
+        }
+        if (!sheared && !dead && nvalid > 0) surv = elim_plain(tb, sbase, nvalid, pm0, sm0);
+        if (surv) hm = strip_corners(tb, sbase, nvalid, surv, prev_pt, has_prev);
         if (args.validate && nvalid > 0) validate_strip(tb, sbase, nvalid, prev_pt, has_prev);
 
         pm_carry = fmaxf(pm_carry, tmax);
@@ -498,6 +634,9 @@ struct Warp {
         const int M = (int)((b - a + C::kT - 1) / C::kT);
         RState R{0, 0, out + a, P};
         pn = 0;
+        xfirst = P[0].x;
+        sh_skip = 0;
+        sh_fail = 0;
         float pm_carry = neg_inf();
         float2 prev_pt = make_float2(0.f, 0.f);
         bool has_prev = false;
@@ -506,6 +645,10 @@ struct Warp {
             has_prev = true;
         }
         const int npre = M < C::kS ? M : C::kS;
+        // The tile buffers may hold generic writes of an earlier merge: order
+        // them before the bulk copies that reuse the buffers.
+        fence_proxy_async_smem();
+        __syncwarp();
         if (lane == 0)
             for (int k = 0; k < npre; ++k) issue(P, a, b, k, seq + k);
         unsigned issued = seq + npre;
@@ -555,6 +698,16 @@ struct Warp {
         }
         bool last = false;
         publish(it, item_index, R, pm_carry, last);
+        if (!last && R.g == 0) {
+            if (args.items) {
+                pair_bridges(it, item_index, count);
+            } else {
+                // single set: after the CTA's warps are done, unless this
+                // CTA merges
+                pp_item = item_index;
+                pp_count = count;
+            }
+        }
         if (last) {
             if (args.items) {
                 // batched: the other warps are busy with other sets; merge alone
@@ -578,7 +731,11 @@ struct Warp {
         const int stage0 = args.items ? args.items[item_index - it.c].pad : 0;
         if (R.g == 0) {
             float2 *dst = ss.xy + (size_t)(stage0 + it.c) * C::kRCap;
-            for (int k = lane; k < R.w; k += 32) dst[k] = rxy()[k];
+            int *dsti = ss.sidx + (size_t)(stage0 + it.c) * C::kRCap;
+            for (int k = lane; k < R.w; k += 32) {
+                dst[k] = rxy()[k];
+                dsti[k] = ridx()[k];
+            }
         }
         if (lane == 0) {
             ss.count[it.slot] = R.g == 0 ? count : -count - 1;  // negative: coordinates not staged
@@ -596,6 +753,36 @@ struct Warp {
         if (last) __threadfence();
     }
 
+    // After publishing segment hood c (staged, `count` corners): for each
+    // neighbour pair (c - 1, c) and (c, c + 1), the second of its two
+    // segments to be published computes the pair's bridge and stores it,
+    // tagged with this call, for the final merge (which computes any pair
+    // bridge it does not find).
+    __device__ __noinline__ void pair_bridges(const SegItem &it, int item_index, int count)
+    {
+        const SegStore ss = store();
+        const float2 *P = reinterpret_cast<const float2 *>(args.points) + it.set_base;
+        const int32_t *out = args.out_idx + it.set_base;
+        const int stage0 = args.items ? args.items[item_index - it.c].pad : 0;
+        for (int side = 0; side < 2; ++side) {
+            const int l = it.c - 1 + side;  // the pair (l, l + 1)
+            if (l < 0 || l + 1 >= it.nseg) continue;
+            unsigned old = 0;
+            if (lane == 0) old = atomicExch(ss.pair + stage0 + l, tag);
+            old = __shfl_sync(kFull, old, 0);
+            if (old != tag) continue;  // the other hood comes later; its warp bridges the pair
+            __threadfence();
+            const int o = side == 0 ? l : l + 1;
+            const int ro = __ldcg(ss.count + it.slot0 + o);
+            if (ro < 0) continue;  // the other hood is not staged
+            const int rl = side == 0 ? ro : count, rr = side == 0 ? count : ro;
+            const int2 pq = bridge_hoods(ss, P, out, stage0, it, item_index, l, rl, l + 1, rr, buf(0));
+            if (lane == 0)
+                __stcg(ss.bridge + stage0 + l,
+                       ((unsigned long long)tag << 32) | ((unsigned long long)pq.x << 16) | (unsigned)pq.y);
+        }
+    }
+
     // ------------------------------------------------------- final merge
     // Corners of published segment hood c: staged coordinates when present,
     // else gathered through the indices in the output array.
@@ -605,6 +792,47 @@ struct Warp {
         const float2 *P;
         __device__ __forceinline__ float2 pt(int j) const { return xy ? __ldcg(xy + j) : P[__ldcg(idx + j)]; }
     };
+
+    // Corners copied into shared memory.
+    struct FlatHood {
+        const float2 *xy;
+        __device__ __forceinline__ float2 pt(int j) const { return xy[j]; }
+    };
+
+    // Bridge of published hoods c (left) and d (right). When both have their
+    // coordinates staged, they are first copied into shared memory at stg
+    // (2 RCAP corners; one round of global loads) and searched there.
+    __device__ int2 bridge_hoods(const SegStore &ss, const float2 *P, const int32_t *out, int stage0,
+                                 const SegItem &it, int item_index, int c, int rc, int d, int rd,
+                                 float2 *stg)
+    {
+        const int hc = rc < 0 ? -rc - 1 : rc, hd = rd < 0 ? -rd - 1 : rd;
+        if (rc >= 0 && rd >= 0) {
+            const float2 *xa = ss.xy + (size_t)(stage0 + c) * C::kRCap;
+            const float2 *xb = ss.xy + (size_t)(stage0 + d) * C::kRCap;
+            constexpr int U = C::kRCap / 32;
+            float2 va[U], vb[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = lane + 32 * u;
+                if (k < hc) va[u] = __ldcg(xa + k);
+                if (k < hd) vb[u] = __ldcg(xb + k);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = lane + 32 * u;
+                if (k < hc) stg[k] = va[u];
+                if (k < hd) stg[C::kRCap + k] = vb[u];
+            }
+            __syncwarp();
+            const int2 pq = bridge_warp<MODE>(pc, FlatHood{stg}, hc, FlatHood{stg + C::kRCap}, hd);
+            __syncwarp();
+            return pq;
+        }
+        const SegHood A = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rc);
+        const SegHood B = seg_hood(ss, P, out, stage0, d, seg_start(it, item_index, d), rd);
+        return bridge_warp<MODE>(pc, A, hc, B, hd);
+    }
 
     __device__ SegHood seg_hood(const SegStore &ss, const float2 *P, const int32_t *out, int stage0, int c,
                                 long long a_c, int raw) const
@@ -630,7 +858,8 @@ struct Warp {
     //     one (its points then lie on or below a segment between two input
     //     points);
     //  2. the bridge (bridge_warp) of every adjacent pair of remaining hoods,
-    //     the pairs spread over the warps;
+    //     the pairs spread over the warps (pairs of neighbouring segments may
+    //     come bridged from publication);
     //  3. hood i keeps its corners from the left bridge's corner s_i to the
     //     right bridge's corner e_i. If s_i > e_i, or s_i == e_i and that
     //     corner is not a strict right turn between the two bridges, every
@@ -640,6 +869,8 @@ struct Warp {
     //  4. the kept ranges are compacted into the output (mam 6).
     // The resulting chain is strictly convex, runs from the first point to the
     // last and has every input point on or below it: it is the upper hood.
+    // With the whole CTA, the remaining hoods' coordinates are copied into
+    // shared memory once when they fit, and stages 2-3 run there.
     __device__ __noinline__ void merge_set(const SegItem &it, int item_index, int nw, int gw)
     {
         const float2 *P = reinterpret_cast<const float2 *>(args.points) + it.set_base;
@@ -653,38 +884,88 @@ struct Warp {
         auto sync = [&]() {
             if (cta) __syncthreads(); else __syncwarp();
         };
-        // scratch: 12 nh + 8 ints
+        // staging of bridge operands: 2 RCAP corners per warp, at the end of
+        // the CTA's warp regions (CTA) or in tile buffer 0 (one warp)
+        unsigned char *cta_base = base - C::kWarpBytes * (threadIdx.x >> 5);
+        constexpr size_t kStg = 2 * C::kRCap * sizeof(float2);
+        constexpr size_t kCtaBytes = C::kWarpBytes * C::kW;
+        float2 *stg = cta ? reinterpret_cast<float2 *>(cta_base + kCtaBytes - (size_t)(gw + 1) * kStg) : buf(0);
+        // scratch: 13 nh + 2 ints, 3 x 32 cross-warp words, 8 control words
         int *sm;
-        const size_t need = (size_t)(12 * nh + 8) * 4;
-        if (cta && need <= C::kWarpBytes * C::kW) sm = reinterpret_cast<int *>(base - C::kWarpBytes * (threadIdx.x >> 5));
+        const size_t need = (size_t)(13 * nh + 2 + 96 + 8) * 4;
+        if (cta && need + C::kW * kStg <= kCtaBytes) sm = reinterpret_cast<int *>(cta_base);
         else if (!cta && need <= (size_t)(C::kS - 2) * C::kBuf * 8) sm = reinterpret_cast<int *>(buf(2));
-        else sm = ss.live + (size_t)stage0 * 16;  // 16 ints per segment, >= 12 nh + 8 for nh >= 2
+        else sm = ss.live + (size_t)stage0 * 16;  // 16 ints per segment: >= 13 nh + 106 once nh >= 36,
+                                                   // and smaller sets always fit the shared scratch
         float *yv = reinterpret_cast<float *>(sm);
         int *rv = sm + nh;
         int *lidA = sm + 2 * nh, *bpA = sm + 3 * nh, *bqA = sm + 4 * nh, *pvA = sm + 5 * nh;
         int *lidB = sm + 6 * nh, *bpB = sm + 7 * nh, *bqB = sm + 8 * nh, *pvB = sm + 9 * nh;
         int *dead = sm + 10 * nh;
         int *pos = sm + 11 * nh;  // nh + 1
-        int *ctl = sm + 12 * nh + 1;  // [0] = live count, [1] = any dropped
+        int *hb = sm + 12 * nh + 1;  // nh + 1: offset of segment c's hood in the shared store
+        float *xpre = reinterpret_cast<float *>(sm + 13 * nh + 2);
+        float *xsuf = xpre + 32;
+        int *xsum = reinterpret_cast<int *>(xpre + 64);
+        int *ctl = xsum + 32;  // [0] = live count, [1] = some kept hood not staged, [2] = hoods in shared memory
+        // hood coordinate store: shared memory between the scratch and the
+        // staging areas (whole CTA only)
+        const size_t store_off = (need + 15) / 16 * 16;
+        float2 *hstore = reinterpret_cast<float2 *>(cta_base + store_off);
+        const long long store_cap =
+            (cta && sm == reinterpret_cast<int *>(cta_base)) ? (long long)(kCtaBytes - C::kW * kStg - store_off) / 8
+                                                             : 0;
 
-        // 0. metadata
-        for (int c = t; c < nh; c += nthreads) {
-            yv[c] = __ldcg(ss.ymax + slot0 + c);
-            rv[c] = __ldcg(ss.count + slot0 + c);
-        }
-        sync();
-        // 1. hood staircase (first warp): lane-contiguous blocks
-        if (gw == 0) {
-            const int nb = (nh + 31) >> 5;
-            const int c0 = min(nh, lane * nb), c1 = min(nh, c0 + nb);
+        // Block-wide scans over threads, in thread order.
+        auto excl_sum = [&](int v, int &total) {
+            const int incl = warp_incl_sum(v);
+            if (lane == 31) xsum[gw] = incl;
+            sync();
+            int before = incl - v;
+            total = 0;
+            for (int w = 0; w < nw; ++w) {
+                const int x = xsum[w];
+                if (w < gw) before += x;
+                total += x;
+            }
+            sync();
+            return before;
+        };
+
+        // 1. hood staircase: each thread a block of consecutive segments
+        int nl = 0;
+        {
+            const int m = (nh + nthreads - 1) / nthreads;
+            const int c0 = min(nh, t * m), c1 = min(nh, c0 + m);
             float bm = neg_inf();
-            for (int c = c0; c < c1; ++c) bm = fmaxf(bm, yv[c]);
-            const float ipre = warp_incl_prefix_max(bm);
-            const float isuf = warp_incl_suffix_max(bm);
-            float before = __shfl_up_sync(kFull, ipre, 1);
-            float later = __shfl_down_sync(kFull, isuf, 1);
+            for (int cb = c0; cb < c1; cb += 8) {
+                float y[8];
+                int r[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (cb + u < c1) {
+                        y[u] = __ldcg(ss.ymax + slot0 + cb + u);
+                        r[u] = __ldcg(ss.count + slot0 + cb + u);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (cb + u < c1) {
+                        yv[cb + u] = y[u];
+                        rv[cb + u] = r[u];
+                        bm = fmaxf(bm, y[u]);
+                    }
+                }
+            }
+            const float ip = warp_incl_prefix_max(bm), is = warp_incl_suffix_max(bm);
+            if (lane == 31) xpre[gw] = ip;
+            if (lane == 0) xsuf[gw] = is;
+            sync();
+            float before = __shfl_up_sync(kFull, ip, 1), later = __shfl_down_sync(kFull, is, 1);
             if (lane == 0) before = neg_inf();
             if (lane == 31) later = neg_inf();
+            for (int w = 0; w < gw; ++w) before = fmaxf(before, xpre[w]);
+            for (int w = gw + 1; w < nw; ++w) later = fmaxf(later, xsuf[w]);
             // later maxima, right to left, kept in dead[] for now
             for (int c = c1 - 1; c >= c0; --c) {
                 dead[c] = __float_as_int(later);
@@ -700,18 +981,80 @@ struct Warp {
                 nk += keep;
                 before = fmaxf(before, ym);
             }
-            const int incl = warp_incl_sum(nk);
-            int k = incl - nk;
+            int k = excl_sum(nk, nl);
             for (int c = c0; c < c1; ++c)
                 if (pos[c]) {
                     lidA[k] = c;
                     pvA[k] = 0;
                     ++k;
                 }
-            if (lane == 31) ctl[0] = incl;
         }
         sync();
-        int nl = ctl[0];
+        // bridges of adjacent segments already computed at publication, and
+        // the sizes of the remaining hoods
+        {
+            const int m = (nl + nthreads - 1) / nthreads;
+            const int i0 = min(nl, t * m), i1 = min(nl, i0 + m);
+            int hs = 0;
+            bool unstaged = false;
+            for (int i = i0; i < i1; ++i) {
+                const int c = lidA[i];
+                const int r = rv[c];
+                hs += r < 0 ? -r - 1 : r;
+                unstaged |= r < 0;
+                if (i + 1 < nl && lidA[i + 1] == c + 1) {
+                    const unsigned long long w = __ldcg(ss.bridge + stage0 + c);
+                    if ((unsigned)(w >> 32) == tag) {
+                        bpA[i] = (int)((w >> 16) & 0xffffu);
+                        bqA[i] = (int)(w & 0xffffu);
+                        pvA[i] = 1;
+                    }
+                }
+            }
+            const bool any_unstaged = cta ? __syncthreads_or(unstaged) : __any_sync(kFull, unstaged);
+            int htot = 0;
+            int off = excl_sum(hs, htot);
+            const bool smem = !any_unstaged && htot <= store_cap;
+            if (smem) {
+                for (int i = i0; i < i1; ++i) {
+                    const int c = lidA[i];
+                    hb[c] = off;
+                    off += rv[c];
+                    pos[i] = hb[c];
+                }
+                if (t == 0) pos[nl] = htot;
+                sync();
+                // copy: corner e belongs to the hood i with pos[i] <= e < pos[i + 1]
+                constexpr int U = 4;
+                for (int e0 = t; e0 < htot; e0 += nthreads * U) {
+                    float2 v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * nthreads;
+                        if (e < htot) {
+                            int lo = 0, hi = nl - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (pos[mid] <= e) lo = mid; else hi = mid - 1;
+                            }
+                            v[u] = __ldcg(ss.xy + (size_t)(stage0 + lidA[lo]) * C::kRCap + (e - pos[lo]));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * nthreads;
+                        if (e < htot) hstore[e] = v[u];
+                    }
+                }
+            }
+            if (t == 0) ctl[2] = smem;
+        }
+        sync();
+        const bool smem = ctl[2] != 0;
+        auto corner = [&](int c, int j) -> float2 {
+            if (smem) return hstore[hb[c] + j];
+            return seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rv[c]).pt(j);
+        };
         int *lid = lidA, *bp = bpA, *bq = bqA, *pv = pvA;
         int *lid2 = lidB, *bp2 = bpB, *bq2 = bqB, *pv2 = pvB;
 
@@ -720,11 +1063,11 @@ struct Warp {
             for (int i = gw; i < nl - 1; i += nw) {
                 if (pv[i]) continue;
                 const int c = lid[i], d = lid[i + 1];
-                const int rc = rv[c], rd = rv[d];
-                const int hc = rc < 0 ? -rc - 1 : rc, hd = rd < 0 ? -rd - 1 : rd;
-                const SegHood A = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rc);
-                const SegHood B = seg_hood(ss, P, out, stage0, d, seg_start(it, item_index, d), rd);
-                const int2 pq = bridge_warp<MODE>(pc, A, hc, B, hd);
+                int2 pq;
+                if (smem)
+                    pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[c]}, rv[c], FlatHood{hstore + hb[d]}, rv[d]);
+                else
+                    pq = bridge_hoods(ss, P, out, stage0, it, item_index, c, rv[c], d, rv[d], stg);
                 if (lane == 0) {
                     bp[i] = pq.x;
                     bq[i] = pq.y;
@@ -741,10 +1084,9 @@ struct Warp {
                     if (si > ei) {
                         dd = 1;
                     } else if (si == ei) {
-                        const int c = lid[i], l = lid[i - 1], r = lid[i + 1];
-                        const float2 A = seg_hood(ss, P, out, stage0, l, seg_start(it, item_index, l), rv[l]).pt(bp[i - 1]);
-                        const float2 B = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rv[c]).pt(si);
-                        const float2 Cc = seg_hood(ss, P, out, stage0, r, seg_start(it, item_index, r), rv[r]).pt(bq[i]);
+                        const float2 A = corner(lid[i - 1], bp[i - 1]);
+                        const float2 B = corner(lid[i], si);
+                        const float2 Cc = corner(lid[i + 1], bq[i]);
                         dd = orient<MODE>(pc, A, B, Cc) >= 0;
                     }
                 }
@@ -755,37 +1097,28 @@ struct Warp {
             if (!any) break;
             // compaction of the live list; a pair's bridge stays valid when
             // its two hoods were already adjacent
-            if (gw == 0) {
-                int k = 0;
-                int prev_old = -2;
-                for (int b0 = 0; b0 < nl; b0 += 32) {
-                    const int i = b0 + lane;
-                    const bool alive = i < nl && !dead[i];
-                    const unsigned am = __ballot_sync(kFull, alive);
-                    const int r = __popc(am & ((1u << lane) - 1u));
-                    // old index of the alive hood just before me
-                    const int hi_prev = 31 - __clz(am & ((1u << lane) - 1u));
-                    int prev = hi_prev >= 0 ? b0 + hi_prev : prev_old;
-                    if (alive) {
-                        lid2[k + r] = lid[i];
-                        // pair (k + r - 1, k + r) valid iff the previous alive hood is i - 1
-                        if (k + r > 0) {
-                            const bool ok = prev == i - 1 && pv[i - 1];
-                            pv2[k + r - 1] = ok ? 1 : 0;
-                            if (ok) {
-                                bp2[k + r - 1] = bp[i - 1];
-                                bq2[k + r - 1] = bq[i - 1];
-                            }
-                        }
+            {
+                const int m = (nl + nthreads - 1) / nthreads;
+                const int i0 = min(nl, t * m), i1 = min(nl, i0 + m);
+                int na = 0;
+                for (int i = i0; i < i1; ++i) na += !dead[i];
+                int total = 0;
+                int k = excl_sum(na, total);
+                for (int i = i0; i < i1; ++i) {
+                    if (dead[i]) continue;
+                    lid2[k] = lid[i];
+                    // pair (k, k + 1) stays bridged iff the next alive hood is i + 1
+                    if (i + 1 < nl && !dead[i + 1] && pv[i]) {
+                        pv2[k] = 1;
+                        bp2[k] = bp[i];
+                        bq2[k] = bq[i];
+                    } else {
+                        pv2[k] = 0;
                     }
-                    if (am) prev_old = b0 + 31 - __clz(am);
-                    k += __popc(am);
-                    __syncwarp();
+                    ++k;
                 }
-                if (lane == 0) ctl[0] = k;
+                nl = total;
             }
-            sync();
-            nl = ctl[0];
             int *tmp;
             tmp = lid; lid = lid2; lid2 = tmp;
             tmp = bp; bp = bp2; bp2 = tmp;
@@ -795,18 +1128,22 @@ struct Warp {
         }
 
         // 4. output: ranges [s_i, e_i] of the kept hoods, packed in order.
-        if (gw == 0) {
-            const int nb = (nl + 31) >> 5;
-            const int i0 = min(nl, lane * nb), i1 = min(nl, i0 + nb);
+        int total_out = 0;
+        bool any_unstaged = false;
+        {
+            const int m = (nl + nthreads - 1) / nthreads;
+            const int i0 = min(nl, t * m), i1 = min(nl, i0 + m);
             int sum = 0;
+            bool unstaged = false;
             for (int i = i0; i < i1; ++i) {
                 const int r = rv[lid[i]];
                 const int hi = r < 0 ? -r - 1 : r;
                 const int si = i > 0 ? bq[i - 1] : 0, ei = i < nl - 1 ? bp[i] : hi - 1;
                 sum += ei - si + 1;
+                unstaged |= r < 0;
             }
-            const int incl = warp_incl_sum(sum);
-            int run = incl - sum;
+            any_unstaged = cta ? __syncthreads_or(unstaged) : __any_sync(kFull, unstaged);
+            int run = excl_sum(sum, total_out);
             for (int i = i0; i < i1; ++i) {
                 pos[i] = run;
                 const int r = rv[lid[i]];
@@ -814,14 +1151,43 @@ struct Warp {
                 const int si = i > 0 ? bq[i - 1] : 0, ei = i < nl - 1 ? bp[i] : hi - 1;
                 run += ei - si + 1;
             }
-            if (lane == 31) pos[nl] = incl;
+            if (t == 0) pos[nl] = total_out;
         }
         sync();
+        int ncopy = nl;
+        if (!any_unstaged) {
+            // Every kept hood has its indices staged: copy from there, all
+            // corners at once (element e belongs to the hood i with
+            // pos[i] <= e < pos[i + 1]).
+            constexpr int U = 8;
+            for (int e0 = t; e0 < total_out; e0 += nthreads * U) {
+                int v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthreads;
+                    if (e < total_out) {
+                        int lo = 0, hi = nl - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (pos[mid] <= e) lo = mid; else hi = mid - 1;
+                        }
+                        const int si = lo > 0 ? bq[lo - 1] : 0;
+                        v[u] = __ldcg(ss.sidx + (size_t)(stage0 + lid[lo]) * C::kRCap + si + (e - pos[lo]));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + u * nthreads;
+                    if (e < total_out) out[e] = v[u];
+                }
+            }
+            ncopy = 0;  // nothing left for the batched copy below
+        }
         // Copy in batches [i0, i1) whose destinations all lie below every
         // source in the batch (destinations never exceed sources); batches run
         // one after the other.
         int i0 = 0;
-        while (i0 < nl) {
+        while (i0 < ncopy) {
             const long long a0 = seg_start(it, item_index, lid[i0]) + (i0 > 0 ? bq[i0 - 1] : 0);
             int i1 = i0 + 1;
             while (i1 < nl && (long long)pos[i1 + 1] <= a0) ++i1;
@@ -847,7 +1213,7 @@ struct Warp {
             i0 = i1;
         }
         if (t == 0) {
-            args.out_count[it.set] = pos[nl];
+            args.out_count[it.set] = total_out;
             args.arrivals[it.set] = 0;
         }
         sync();
@@ -873,19 +1239,23 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
     if (threadIdx.x == 0) *Wk.cta_flag() = 0;
     __syncthreads();
 
+    Wk.tag = (__ldcg(&args.hdr->epoch) + 1u) ^ kTagMix;
+    Wk.pp_item = -1;
+
     // Test hook: one bounded wait on a barrier that nothing completes.
+    bool go = true;
     const int stall = args.hdr->stall_test_ns;
     if (stall > 0) {
         bool tmo = false;
         if (lane == 0) tmo = !mbar_wait_bounded(bars + C::kS, 0, (uint64_t)stall);
-        if (__any_sync(kFull, tmo)) {
-            if (lane == 0) record_status(&args.hdr->status, kStTimeout);
-            return;
-        }
+        if (tmo) record_status(&args.hdr->status, kStTimeout);
+        go = !__syncthreads_or(tmo);
     }
 
     unsigned seq = 0;
-    if (args.queue) {
+    if (!go) {
+        // skipped
+    } else if (args.queue) {
         // Batched: every warp takes items from a shared queue (the planning
         // kernel puts the large sets first) until it runs dry.
         const int nitems = *args.num_items_dev;
@@ -913,7 +1283,12 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
         // segment hoods with all its warps (every other warp is done).
         __syncthreads();
         const int flag = *Wk.cta_flag();
+        if (!flag && Wk.pp_item >= 0) Wk.pair_bridges(Wk.item(Wk.pp_item), Wk.pp_item, Wk.pp_count);
         if (flag) {
+            // the merge reuses the CTA's shared memory, barriers included
+            if (lane == 0)
+                for (int s = 0; s <= C::kS; ++s) mbar_inval(bars + s);
+            __syncthreads();
             __threadfence();
             const SegItem it = Wk.item(flag - 1);
             Wk.merge_set(it, flag - 1, C::kW, warp);
@@ -930,6 +1305,18 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
         if (lane == 0) {
             atomicAdd(&args.hdr->tests, t);
             atomicAdd(&args.hdr->fallbacks, f);
+        }
+    }
+
+    // The last CTA to finish advances the workspace's call counter: every
+    // CTA read it at its start, and every tagged word of this call is
+    // written by then.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&args.hdr->done_ctas, 1u) == gridDim.x - 1) {
+            args.hdr->done_ctas = 0;
+            args.hdr->epoch = args.hdr->epoch + 1u;
         }
     }
 }

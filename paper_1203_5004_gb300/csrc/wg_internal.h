@@ -13,7 +13,9 @@ struct WsHeader {
                                    // mbarrier that nothing completes, for this many ns
     unsigned long long tests;      // orientation tests (count_predicates = 1)
     unsigned long long fallbacks;  // float64 recomputations (count_predicates = 1)
-    unsigned long long pad[29];
+    unsigned long long pad[28];
+    unsigned epoch;                // calls completed on this workspace (tags of this call: epoch + 1)
+    unsigned done_ctas;            // CTAs of the running call that have finished
 };
 static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
@@ -48,7 +50,11 @@ struct FusedArgs {
     int *seg_count;          // one per segment slot (negative: coordinates not staged)
     float *seg_ymax;         // one per segment slot: max y of the segment
     float *seg_xy;           // per stage slot: kStageCorners float2 (segment hood coordinates)
+    int *seg_sidx;           // per stage slot: kStageCorners ints (segment hood indices, set-relative)
     int *seg_live;           // per stage slot: 16 ints of final-merge scratch
+    unsigned *seg_pair;      // per stage slot: tag of the call whose segment hood (this or the next
+                             // segment) was published first, for the pair (this, next)
+    unsigned long long *seg_bridge;  // per stage slot: bridge of the pair (this, next): tag << 32 | p << 16 | q
     unsigned *arrivals;      // one per set
 };
 

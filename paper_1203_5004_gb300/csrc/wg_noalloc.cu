@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -36,18 +37,24 @@ using namespace wg;
 
 namespace {
 
-// Layout of the fixed workspace: header | arrivals | per segment: count, max
-// y, merge scratch (16 ints), staged hood coordinates (kStageCorners).
+// Layout of the fixed workspace: header (the set's arrival count sits in its
+// spare words) | per segment: count, max y, merge scratch (16 ints), staged
+// hood coordinates and indices (kStageCorners), pair word, pair bridge.
 constexpr int kNoAllocSegments = 2048;
-constexpr size_t kNaOffArrivals = 256;
-constexpr size_t kNaOffCount = 512;
+constexpr size_t kNaOffArrivals = offsetof(WsHeader, pad);
+constexpr size_t kNaOffCount = 256;
 constexpr size_t kNaOffYmax = kNaOffCount + 4 * (size_t)kNoAllocSegments;
 constexpr size_t kNaOffLive = kNaOffYmax + 4 * (size_t)kNoAllocSegments;
 constexpr size_t kNaOffXy = kNaOffLive + 64 * (size_t)kNoAllocSegments;
-constexpr size_t kNaBytes = kNaOffXy + 8 * (size_t)kStageCorners * kNoAllocSegments;  // about 2.2 MB
+constexpr size_t kNaOffSidx = kNaOffXy + 8 * (size_t)kStageCorners * kNoAllocSegments;
+constexpr size_t kNaOffPair = kNaOffSidx + 4 * (size_t)kStageCorners * kNoAllocSegments;
+constexpr size_t kNaOffBridge = kNaOffPair + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaBytes = kNaOffBridge + 8 * (size_t)kNoAllocSegments;  // about 3.3 MB
 // Bytes that every call must see as zero: the status word, the counters and
-// the arrival count of the last-segment merge.
-constexpr size_t kNaZeroBytes = kNaOffCount;
+// the arrival count of the last-segment merge. The call counter after them
+// (and the pair words it tags) must survive from call to call.
+constexpr size_t kNaZeroBytes = offsetof(WsHeader, epoch);
+static_assert(kNaOffArrivals + 4 <= kNaZeroBytes, "arrival count inside the cleared header words");
 constexpr int kNaTileCfg = 3;
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNaBytes];
@@ -118,5 +125,8 @@ extern "C" wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32
     a.seg_ymax = reinterpret_cast<float *>(w + kNaOffYmax);
     a.seg_live = reinterpret_cast<int *>(w + kNaOffLive);
     a.seg_xy = reinterpret_cast<float *>(w + kNaOffXy);
+    a.seg_sidx = reinterpret_cast<int *>(w + kNaOffSidx);
+    a.seg_pair = reinterpret_cast<unsigned *>(w + kNaOffPair);
+    a.seg_bridge = reinterpret_cast<unsigned long long *>(w + kNaOffBridge);
     return fused_launch(kNaTileCfg, a, grid, 0, s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 }
