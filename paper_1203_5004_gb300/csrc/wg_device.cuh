@@ -47,9 +47,15 @@ enum : int { kModeFp64Only = 1, kModeCount = 2 };
 // S = fl(|t1| + |t2|) >= (|t1| + |t2|) / (1 + u), and B = 2^-22 S is exact,
 // so |D| > B implies |D| > 2u (|t1| + |t2|) >= |D - det|: sign(D) = sign(det)
 // and det != 0. No underflow occurs: a nonzero product of grid differences is
-// at least 2^-48. Otherwise the determinant is recomputed in float64, where
-// both products (48 significant bits) and their difference (49 bits) are
-// exact. The __f*_rn / __d*_rn intrinsics are never contracted into FMAs.
+// at least 2^-48. The bound is zero when nothing was rounded: both exact
+// products are integer multiples of 2^-48, so if max(|t1|, |t2|) < 2^-25
+// (rounding is monotone and 2^-25 is a float, so the exact products are below
+// it too) they have fewer than 23 significant bits and are exact, and their
+// difference, a multiple of 2^-48 below 2^-24, is exact as well: D = det and
+// its sign, zero included, is final. Otherwise, when |D| <= B, the
+// determinant is recomputed in float64, where both products (48 significant
+// bits) and their difference (49 bits) are exact. The __f*_rn / __d*_rn
+// intrinsics are never contracted into FMAs.
 // ---------------------------------------------------------------------------
 struct PredCount {
     unsigned long long tests = 0;
@@ -66,6 +72,7 @@ __device__ __forceinline__ int orient(PredCount &pc, float2 o, float2 a, float2 
         const float t1 = __fmul_rn(dx1, dy2);
         const float t2 = __fmul_rn(dy1, dx2);
         const float d = __fsub_rn(t1, t2);
+        if (fmaxf(fabsf(t1), fabsf(t2)) < 0x1p-25f) return (d > 0.f) - (d < 0.f);  // exact
         const float bound = __fmul_rn(__fadd_rn(fabsf(t1), fabsf(t2)), 0x1p-22f);
         if (fabsf(d) > bound) return d > 0.f ? 1 : -1;
         if (MODE & kModeCount) pc.fallbacks++;

@@ -420,7 +420,7 @@ struct Warp {
     // after it is strictly higher. pm0 / sm0: max height before / after the
     // strip. Returns the mask of the strip's points that remain.
     __device__ __forceinline__ unsigned elim_plain(const float2 *tb, int sbase, int nvalid, float pm0,
-                                                   float sm0) const
+                                                   float sm0, float2 prev_pt, bool has_prev) const
     {
         constexpr int K = C::kK;
         float py[K];
@@ -440,7 +440,36 @@ struct Warp {
             if (!(((kpre >> j) & 1u) && py[j] < smx)) surv |= 1u << j;
             smx = fmaxf(smx, py[j]);
         }
-        return surv & (nvalid >= K ? ((1u << K) - 1u) : ((1u << nvalid) - 1u));
+        surv &= nvalid >= K ? ((1u << K) - 1u) : ((1u << nvalid) - 1u);
+        if (__popc(surv) > 2) surv &= ~column_mask(tb, sbase, nvalid, prev_pt, has_prev);
+        return surv;
+    }
+
+    // The column rule (as in strip_corners) on a whole strip: the mask of
+    // its points that have a strictly higher point directly above them and
+    // either a point below them in their column or the set's first column to
+    // their left. Point j - 1 is tested when point j is loaded.
+    __device__ __forceinline__ unsigned column_mask(const float2 *tb, int sbase, int nvalid, float2 prev_pt,
+                                                    bool has_prev) const
+    {
+        constexpr int K = C::kK;
+        const float nan = __int_as_float(0x7fffffff);
+        unsigned col = 0;
+        float xb = sbase > 0 ? tb[sbase - 1].x : (has_prev ? prev_pt.x : nan);
+        float xa = nan, ya = 0.f;
+#pragma unroll 4
+        for (int j = 0; j <= K; ++j) {
+            const float2 v = j < nvalid ? tb[sbase + j] : make_float2(nan, 0.f);
+            if (j > 0) {
+                const bool up = v.x == xa && v.y > ya;
+                const bool left = xb == xa || xa > xfirst;
+                col |= (up && left ? 1u : 0u) << (j - 1);
+                xb = xa;
+            }
+            xa = v.x;
+            ya = v.y;
+        }
+        return col;
     }
 
     // The strip's corners among the points that remain (surv): first
@@ -530,84 +559,170 @@ struct Warp {
 
     // ------------------------------------------------ one tile, decided
     // Tile at tb (cnt points, the first at set-relative index `start`);
-    // ymax_mine = max y of this lane's strip; ynext = max y of the look-ahead
-    // tile (or -inf). If IDX_SMEM the input indices are in idx_arr, else
-    // start + position. Survivor corners go to the pending list.
-    template <bool IDX_SMEM>
-    __device__ __forceinline__ void decide(const float2 *tb, int cnt, long long start, const int *idx_arr,
-                                           float ymax_mine, float ynext, float &pm_carry, float2 &prev_pt,
-                                           bool &has_prev, RState &R)
+    // ymax_mine = max y of this lane's strip, tmax = max y of the tile, ynext
+    // = max y of the look-ahead tile (or -inf). Survivor corners go to the
+    // pending list.
+    __device__ __forceinline__ void decide(const float2 *tb, int cnt, long long start, float ymax_mine, float tmax,
+                                           float ynext, float &pm_carry, float2 &prev_pt, bool &has_prev,
+                                           RState &R)
     {
         constexpr int K = C::kK;
-        const float ipre = warp_incl_prefix_max(ymax_mine);
-        const float isuf = warp_incl_suffix_max(ymax_mine);
-        float epre = __shfl_up_sync(kFull, ipre, 1);
-        float esuf = __shfl_down_sync(kFull, isuf, 1);
-        if (lane == 0) epre = neg_inf();
-        if (lane == 31) esuf = neg_inf();
-        const float tmax = __shfl_sync(kFull, ipre, 31);
-        const float pm0 = fmaxf(pm_carry, epre);
-        const float sm0 = fmaxf(esuf, ynext);
-
         const int sbase = lane * K;
         const int nvalid = cnt - sbase;
-        unsigned hm = 0;
         // Whole strip dropped: everything before it is at least as high as its
-        // maximum, and something after it is strictly higher.
+        // maximum (pm0), and something after it is strictly higher (sm0).
+        float pm0, sm0;
+        if (tmax <= pm_carry) {
+            // the tile's own earlier strips add nothing to pm_carry
+            pm0 = pm_carry;
+            if (tmax < ynext) {
+                sm0 = ynext;
+            } else {
+                const float isuf = warp_incl_suffix_max(ymax_mine);
+                float esuf = __shfl_down_sync(kFull, isuf, 1);
+                if (lane == 31) esuf = neg_inf();
+                sm0 = fmaxf(esuf, ynext);
+            }
+        } else {
+            const float ipre = warp_incl_prefix_max(ymax_mine);
+            const float isuf = warp_incl_suffix_max(ymax_mine);
+            float epre = __shfl_up_sync(kFull, ipre, 1);
+            float esuf = __shfl_down_sync(kFull, isuf, 1);
+            if (lane == 0) epre = neg_inf();
+            if (lane == 31) esuf = neg_inf();
+            pm0 = fmaxf(pm_carry, epre);
+            sm0 = fmaxf(esuf, ynext);
+        }
         const bool dead = !(ymax_mine > pm0) && ymax_mine < sm0;
         const unsigned live = __ballot_sync(kFull, !dead && nvalid > 0);
-        unsigned surv = 0;
-        bool sheared = false;
-        if (sh_skip > 0) {
-            --sh_skip;
-        } else if (__popc(live) > kShearLanes) {
-            // Many strips survive: try the sheared frame. After a trial that
-            // does not pay, skip the next 2, 4, ... 64 tiles' trials.
-            const unsigned long long r = sheared_tile<K>(tb, cnt, nvalid, __popc(live), prev_pt, has_prev);
-            if (r >> 32) {
-                sheared = true;
-                surv = (unsigned)r;
-                sh_fail = 0;
-            } else {
-                sh_fail = min(sh_fail + 1, 6);
-                sh_skip = 1 << sh_fail;
+        unsigned hm = 0;
+        if (live) {
+            unsigned surv = 0;
+            bool sheared = false, done = false;
+            if (sh_skip > 0) {
+                --sh_skip;
+            } else if (__popc(live) > kShearLanes) {
+                // Many strips survive: try the sheared frame. After a trial
+                // that does not pay, skip the next 2, 4, ... 64 tiles' trials.
+                const unsigned long long r = sheared_tile<K>(tb, cnt, nvalid, __popc(live), prev_pt, has_prev);
+                if (r >> 32) {
+                    sheared = true;
+                    surv = (unsigned)r;
+                    sh_fail = 0;
+                } else {
+                    sh_fail = min(sh_fail + 1, 6);
+                    sh_skip = 1 << sh_fail;
+                }
             }
+            if (!sheared && __popc(live) == 1) {
+                // One strip survives: the whole warp tests its points, one per lane.
+                const int L = __ffs(live) - 1;
+                const unsigned S = strip_survivors_warp(tb, cnt, L, __shfl_sync(kFull, pm0, L),
+                                                        __shfl_sync(kFull, sm0, L), prev_pt, has_prev);
+                if (lane == L) {
+                    surv = S;
+                    // a hood of at most two points is the points themselves
+                    if (__popc(S) <= 2) {
+                        hm = S;
+                        done = true;
+                    }
+                }
+            } else if (!sheared && !dead && nvalid > 0) {
+                surv = elim_plain(tb, sbase, nvalid, pm0, sm0, prev_pt, has_prev);
+            }
+            if (surv && !done) hm = strip_corners(tb, sbase, nvalid, surv, prev_pt, has_prev);
         }
-        if (!sheared && !dead && nvalid > 0) surv = elim_plain(tb, sbase, nvalid, pm0, sm0);
-        if (surv) hm = strip_corners(tb, sbase, nvalid, surv, prev_pt, has_prev);
         if (args.validate && nvalid > 0) validate_strip(tb, sbase, nvalid, prev_pt, has_prev);
 
         pm_carry = fmaxf(pm_carry, tmax);
         prev_pt = tb[cnt - 1];
         has_prev = true;
 
+        const unsigned with = __ballot_sync(kFull, hm != 0);
+        if (!with) return;
         const int hc = __popc(hm);
-        if (__any_sync(kFull, hc > 0)) {
-            const int incl = warp_incl_sum(hc);
-            const int m = __shfl_sync(kFull, incl, 31);
-            const int rank0 = incl - hc;
-            for (int r0 = 0; r0 < m;) {
-                if (pn == C::kPCap) flush_pending(R);
-                const int take = min(C::kPCap - pn, m - r0);
-                if (hm) {
-                    int r = rank0;
+        if (__popc(with) == 1) {
+            // one lane holds all the corners: it appends them itself
+            const int L = __ffs(with) - 1;
+            const int m = __shfl_sync(kFull, hc, L);
+            if (pn + m <= C::kPCap) {
+                if (lane == L) {
+                    int r = pn;
                     unsigned bits = hm;
                     while (bits) {
                         const int j = __ffs(bits) - 1;
                         bits &= bits - 1;
-                        if (r >= r0 && r < r0 + take) {
-                            pxy()[pn + r - r0] = tb[sbase + j];
-                            pidx()[pn + r - r0] = IDX_SMEM ? idx_arr[sbase + j] : (int)(start + sbase + j);
-                        }
+                        pxy()[r] = tb[sbase + j];
+                        pidx()[r] = (int)(start + sbase + j);
                         ++r;
                     }
                 }
                 __syncwarp();
-                pn += take;
-                r0 += take;
+                pn += m;
+                if (pn >= 32) flush_pending(R);
+                return;
             }
-            if (pn >= 32) flush_pending(R);
         }
+        const int incl = warp_incl_sum(hc);
+        const int m = __shfl_sync(kFull, incl, 31);
+        const int rank0 = incl - hc;
+        for (int r0 = 0; r0 < m;) {
+            if (pn == C::kPCap) flush_pending(R);
+            const int take = min(C::kPCap - pn, m - r0);
+            if (hm) {
+                int r = rank0;
+                unsigned bits = hm;
+                while (bits) {
+                    const int j = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    if (r >= r0 && r < r0 + take) {
+                        pxy()[pn + r - r0] = tb[sbase + j];
+                        pidx()[pn + r - r0] = (int)(start + sbase + j);
+                    }
+                    ++r;
+                }
+            }
+            __syncwarp();
+            pn += take;
+            r0 += take;
+        }
+        if (pn >= 32) flush_pending(R);
+    }
+
+    // Survivors of strip L of a tile (the only strip not dropped whole),
+    // tested by the whole warp, lane j holding the strip's point j: the
+    // height rule (pm0 / sm0: max height before / after the strip), first
+    // occurrence and the column rule, as elim_plain and strip_corners apply
+    // them. Returns the mask of the strip's remaining points (all lanes).
+    __device__ __forceinline__ unsigned strip_survivors_warp(const float2 *tb, int cnt, int L, float pm0,
+                                                             float sm0, float2 prev_pt, bool has_prev) const
+    {
+        constexpr int K = C::kK;
+        const float nan = __int_as_float(0x7fffffff);
+        const int sb = L * K;
+        const int nv = min(K, cnt - sb);
+        const bool mine = lane < nv;
+        const float2 q = mine ? tb[sb + lane] : make_float2(nan, neg_inf());
+        float2 qp = shfl2(q, (lane + 31) & 31);
+        bool hvp = lane > 0;
+        if (lane == 0 && (sb > 0 || has_prev)) {
+            qp = sb > 0 ? tb[sb - 1] : prev_pt;
+            hvp = true;
+        }
+        float2 qn = shfl2(q, (lane + 1) & 31);
+        if (lane == nv - 1) qn = sb + nv < cnt ? tb[sb + nv] : make_float2(nan, neg_inf());
+        const float ip = warp_incl_prefix_max(q.y), is = warp_incl_suffix_max(q.y);
+        float ep = __shfl_up_sync(kFull, ip, 1), es = __shfl_down_sync(kFull, is, 1);
+        if (lane == 0) ep = neg_inf();
+        if (lane == 31) es = neg_inf();
+        ep = fmaxf(ep, pm0);
+        es = fmaxf(es, sm0);
+        bool keep = mine && !(q.y <= ep && q.y < es);
+        keep = keep && !(hvp && same_point(qp, q));
+        const bool up = qn.x == q.x && qn.y > q.y;
+        const bool left = (hvp && qp.x == q.x) || q.x > xfirst;
+        keep = keep && !(up && left);
+        return __ballot_sync(kFull, keep);
     }
 
     // Wait (bounded) for tiles [from, to) after a timeout, so that no bulk
@@ -654,7 +769,7 @@ struct Warp {
         unsigned issued = seq + npre;
         __syncwarp();
 
-        float ymax_prev = neg_inf();
+        float ymax_prev = neg_inf(), tmax_prev = neg_inf();
         for (int i = 0; i <= M; ++i) {
             float ymax_cur = neg_inf(), ynext = neg_inf();
             if (i < M) {
@@ -675,8 +790,8 @@ struct Warp {
                 const unsigned s = seq + i - 1;
                 const long long st = a + (long long)(i - 1) * C::kT;
                 const int cnt = (int)((b - st) < C::kT ? (b - st) : C::kT);
-                decide<false>(buf(s % C::kS) + tile_shift(P, st), cnt, st, nullptr, ymax_prev, ynext,
-                              pm_carry, prev_pt, has_prev, R);
+                decide(buf(s % C::kS) + tile_shift(P, st), cnt, st, ymax_prev, tmax_prev, ynext, pm_carry,
+                       prev_pt, has_prev, R);
                 __syncwarp();
                 if (i - 1 + C::kS < M) {
                     if (lane == 0) {
@@ -687,6 +802,7 @@ struct Warp {
                 }
             }
             ymax_prev = ymax_cur;
+            tmax_prev = ynext;
         }
         seq += M;
         flush_pending(R);

@@ -67,6 +67,29 @@ def test_orient_signs(wg, mode):
         assert fb < ref.shape[0]
 
 
+def test_orient_small_differences_exact_without_fallback(wg):
+    # All three points within 2^11 grid units of each other: both products are
+    # below 2^23 units of 2^-48, so the float32 determinant is exact (zero
+    # included) and no triple needs the float64 path.
+    r = np.random.default_rng(3)
+    n = 300_000
+    o = r.integers(0, inputs.G - (1 << 11), size=(n, 1, 2))
+    off = r.integers(0, 1 << 11, size=(n, 3, 2))
+    # every third triple exactly collinear: c, c + d, c + m d with m in {0, 1, 2}
+    d = r.integers(-(1 << 5), 1 << 5, size=(n, 2))
+    m = r.integers(0, 3, size=(n, 1))
+    c = np.full_like(d, 1 << 10)
+    col = np.stack([c, c + d, c + m * d], axis=1)
+    pts = np.where((np.arange(n) % 3 == 0)[:, None, None], col, off) + o
+    pts = np.clip(pts.reshape(-1, 2), 0, inputs.G - 1).astype(np.int32)
+    ref = oracle.orient_signs(pts[:, 0], pts[:, 1])
+    assert (ref == 0).sum() > n // 4
+    t = torch.from_numpy(inputs.to_float_points(pts[:, 0], pts[:, 1])).to(DEV)
+    signs, fb = wg.debug_orient(t, pred_mode=0)
+    assert_same(signs.cpu().numpy(), ref, "orient signs, small differences")
+    assert fb == 0
+
+
 # ---------------------------------------------------------------- bridge
 def _hood_pair(r, n, span, kind):
     kx = r.integers(0, span, size=n) * (inputs.G // span if kind == "coarse" else 1)
