@@ -26,7 +26,12 @@ template <int MODE>
 __global__ void dbg_bridge_kernel(const float2 *P, int hp, const float2 *Q, int hq, int *out)
 {
     PredCount pc;
-    const int2 pq = bridge_warp<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);
+    int2 pq = bridge_warp<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);
+    if (hp <= 32 && hq <= 32) {
+        // the small-hood search must give the same bridge
+        const int2 r = bridge_small<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);
+        if (r.x != pq.x || r.y != pq.y) pq = make_int2(-1, -1);
+    }
     if (threadIdx.x == 0) {
         out[0] = pq.x;
         out[1] = pq.y;

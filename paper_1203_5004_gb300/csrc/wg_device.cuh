@@ -203,6 +203,40 @@ __device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int
     return make_int2(lo, q);
 }
 
+// The same bridge for small hoods (1 <= hp, hq <= 32), corners held one per
+// lane: lane i holds P[i] and Q[i]. Every P corner finds its tangent corner on
+// Q by tangent_from's binary search (a fixed ceil(log2 hq) steps for the
+// whole warp, lanes that are done keep their bracket), with Q's corners
+// fetched by shuffles; one round of f votes over all of P then gives the
+// bridge corner: the first corner whose vote is not LOW, else the last one.
+// These are the probes bridge_warp makes when it samples every corner of P,
+// so the result is the same.
+template <int MODE, class PA, class QA>
+__device__ int2 bridge_small(PredCount &pc, const PA &P, int hp, const QA &Q, int hq)
+{
+    const int lane = lane_id();
+    const float2 pi = lane < hp ? P.pt(lane) : make_float2(0.f, 0.f);
+    const float2 qi = lane < hq ? Q.pt(lane) : make_float2(0.f, 0.f);
+    int lo = 0, hi = hq - 1;
+    const int steps = hq > 1 ? 32 - __clz(hq - 1) : 0;
+    for (int k = 0; k < steps; ++k) {
+        const int mid = (lo + hi) >> 1;
+        const float2 a = shfl2(qi, mid), b = shfl2(qi, min(mid + 1, 31));
+        if (lo < hi && lane < hp) {
+            if (orient<MODE>(pc, pi, a, b) >= 0)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+    }
+    const float2 qt = shfl2(qi, lo);
+    const float2 pn = shfl2(pi, (lane + 1) & 31);
+    const bool vote = lane < hp - 1 && !(orient<MODE>(pc, pi, qt, pn) > 0);
+    const unsigned nl = __ballot_sync(kFull, vote);
+    const int p = nl ? __ffs(nl) - 1 : hp - 1;
+    return make_int2(p, __shfl_sync(kFull, lo, p));
+}
+
 // ---------------------------------------------------------------------------
 // Hood of up to 32 sorted, distinct points held one per lane (lanes [0, m)),
 // computed in registers by the paper's stages d = 1, 2, 4, 8, 16: at stage d
@@ -332,6 +366,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// L2 policy for data read once: evicted first, so that a stream much larger
+// than L2 does not push out the workspace, the code and other reused lines.
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// The same bulk copy with an L2 cache policy.
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                              uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 

@@ -266,7 +266,7 @@ struct Warp {
         if (nint > 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, (unsigned)nint * 8u);
-            bulk_g2s(dst + 2 * shift, src + shift, (unsigned)nint * 8u, bar);
+            bulk_g2s_hint(dst + 2 * shift, src + shift, (unsigned)nint * 8u, bar, l2_evict_first_policy());
         } else {
             mbar_arrive(bar);
         }
@@ -909,6 +909,12 @@ struct Warp {
         __device__ __forceinline__ float2 pt(int j) const { return xy ? __ldcg(xy + j) : P[__ldcg(idx + j)]; }
     };
 
+    // Staged corners read from global memory (L2).
+    struct CgHood {
+        const float2 *xy;
+        __device__ __forceinline__ float2 pt(int j) const { return __ldcg(xy + j); }
+    };
+
     // Corners copied into shared memory.
     struct FlatHood {
         const float2 *xy;
@@ -923,6 +929,9 @@ struct Warp {
                                  float2 *stg)
     {
         const int hc = rc < 0 ? -rc - 1 : rc, hd = rd < 0 ? -rd - 1 : rd;
+        if (rc >= 0 && rd >= 0 && hc <= 32 && hd <= 32)
+            return bridge_small<MODE>(pc, CgHood{ss.xy + (size_t)(stage0 + c) * C::kRCap}, hc,
+                                      CgHood{ss.xy + (size_t)(stage0 + d) * C::kRCap}, hd);
         if (rc >= 0 && rd >= 0) {
             const float2 *xa = ss.xy + (size_t)(stage0 + c) * C::kRCap;
             const float2 *xb = ss.xy + (size_t)(stage0 + d) * C::kRCap;
@@ -1106,31 +1115,31 @@ struct Warp {
                 }
         }
         sync();
-        // bridges of adjacent segments already computed at publication, and
-        // the sizes of the remaining hoods
+        // the sizes of the remaining hoods; their corners copied into shared
+        // memory when they fit, and the bridges of adjacent segments already
+        // computed at publication (both in one round of loads)
         {
             const int m = (nl + nthreads - 1) / nthreads;
             const int i0 = min(nl, t * m), i1 = min(nl, i0 + m);
             int hs = 0;
             bool unstaged = false;
             for (int i = i0; i < i1; ++i) {
-                const int c = lidA[i];
-                const int r = rv[c];
+                const int r = rv[lidA[i]];
                 hs += r < 0 ? -r - 1 : r;
                 unstaged |= r < 0;
-                if (i + 1 < nl && lidA[i + 1] == c + 1) {
-                    const unsigned long long w = __ldcg(ss.bridge + stage0 + c);
-                    if ((unsigned)(w >> 32) == tag) {
-                        bpA[i] = (int)((w >> 16) & 0xffffu);
-                        bqA[i] = (int)(w & 0xffffu);
-                        pvA[i] = 1;
-                    }
-                }
             }
             const bool any_unstaged = cta ? __syncthreads_or(unstaged) : __any_sync(kFull, unstaged);
             int htot = 0;
             int off = excl_sum(hs, htot);
             const bool smem = !any_unstaged && htot <= store_cap;
+            constexpr int MB = 2;  // bridge words loaded ahead of the copy, per thread
+            unsigned long long bw[MB];
+#pragma unroll
+            for (int u = 0; u < MB; ++u) {
+                const int i = i0 + u;
+                bw[u] = 0;
+                if (i < i1 && i + 1 < nl && lidA[i + 1] == lidA[i] + 1) bw[u] = __ldcg(ss.bridge + stage0 + lidA[i]);
+            }
             if (smem) {
                 for (int i = i0; i < i1; ++i) {
                     const int c = lidA[i];
@@ -1163,6 +1172,21 @@ struct Warp {
                     }
                 }
             }
+            for (int i = i0; i < i1; ++i) {
+                unsigned long long w = 0;
+                if (i - i0 < MB) {
+#pragma unroll
+                    for (int u = 0; u < MB; ++u)
+                        if (i - i0 == u) w = bw[u];
+                } else if (i + 1 < nl && lidA[i + 1] == lidA[i] + 1) {
+                    w = __ldcg(ss.bridge + stage0 + lidA[i]);
+                }
+                if ((unsigned)(w >> 32) == tag) {
+                    bpA[i] = (int)((w >> 16) & 0xffffu);
+                    bqA[i] = (int)(w & 0xffffu);
+                    pvA[i] = 1;
+                }
+            }
             if (t == 0) ctl[2] = smem;
         }
         sync();
@@ -1180,7 +1204,9 @@ struct Warp {
                 if (pv[i]) continue;
                 const int c = lid[i], d = lid[i + 1];
                 int2 pq;
-                if (smem)
+                if (smem && rv[c] <= 32 && rv[d] <= 32)
+                    pq = bridge_small<MODE>(pc, FlatHood{hstore + hb[c]}, rv[c], FlatHood{hstore + hb[d]}, rv[d]);
+                else if (smem)
                     pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[c]}, rv[c], FlatHood{hstore + hb[d]}, rv[d]);
                 else
                     pq = bridge_hoods(ss, P, out, stage0, it, item_index, c, rv[c], d, rv[d], stg);

@@ -92,8 +92,15 @@ def test_orient_small_differences_exact_without_fallback(wg):
 
 # ---------------------------------------------------------------- bridge
 def _hood_pair(r, n, span, kind):
-    kx = r.integers(0, span, size=n) * (inputs.G // span if kind == "coarse" else 1)
-    ky = r.integers(0, inputs.G, size=n) if kind != "coarse" else r.integers(0, span, size=n) * (inputs.G // span)
+    if kind == "arc":
+        # points on the quantised parabola of the arc workload, in a narrow x
+        # window: long runs of hood corners, near-collinear triples
+        x0 = int(r.integers(0, inputs.G - (1 << 16)))
+        kx = x0 + r.integers(0, 1 << int(r.integers(6, 16)), size=n)
+        ky = inputs._arc_ky(kx)
+    else:
+        kx = r.integers(0, span, size=n) * (inputs.G // span if kind == "coarse" else 1)
+        ky = r.integers(0, inputs.G, size=n) if kind != "coarse" else r.integers(0, span, size=n) * (inputs.G // span)
     kx, ky = inputs.sort_lex(kx, ky)
     key = kx.astype(np.int64) * inputs.G + ky
     _, first = np.unique(key, return_index=True)
@@ -106,12 +113,12 @@ def _hood_pair(r, n, span, kind):
     return kx, ky, hp, hq
 
 
-@pytest.mark.parametrize("kind", ["fine", "coarse"])
+@pytest.mark.parametrize("kind", ["fine", "coarse", "arc"])
 def test_bridge_against_oracle(wg, kind):
-    r = np.random.default_rng(2 if kind == "fine" else 3)
+    r = np.random.default_rng({"fine": 2, "coarse": 3, "arc": 13}[kind])
     checked = 0
     for trial in range(400):
-        n = int(r.integers(2, 3000))
+        n = int(r.integers(2, 3000 if kind != "arc" else 80))
         span = int(r.integers(2, 64)) if kind == "coarse" else inputs.G
         pair = _hood_pair(r, n, span, kind)
         if pair is None:
