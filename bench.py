@@ -281,10 +281,22 @@ def run_batched(args, world, rank, local):
     counts = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
     ws = wagener.new_workspace(wagener.batched_workspace_size(offs), dev)
     stream = torch.cuda.current_stream(dev)
-    step = lambda: wagener.upper_hood_batched_into(pts, offs_d, out, counts, ws)
+    direct = lambda: wagener.upper_hood_batched_into(pts, offs_d, out, counts, ws)
     for _ in range(max(3, args.warmup)):
+        direct()
+    torch.cuda.synchronize(dev)
+    ref_counts = counts.clone()
+    # One step (planning kernel + persistent fused kernel) captured in a CUDA
+    # graph; the workspace's counters reset themselves, so replays are exact.
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        direct()
+    torch.cuda.synchronize(dev)
+    step = graph.replay
+    for _ in range(3):
         step()
     torch.cuda.synchronize(dev)
+    graph_same = bool(torch.equal(counts, ref_counts))
     K = args.steps
     sampler = ClockSampler(local)
     sampler.start()
@@ -294,8 +306,26 @@ def run_batched(args, world, rank, local):
     ms = time_steps(step, K, stream, dev)
     clocks = sampler.stop()
     ms = max_over_ranks(ms, pg, dev)
+    direct_ms = time_steps(direct, K, stream, dev)
     value = S * world / (ms * 1e-3)
     hsum = int(counts.sum().item())
+
+    # End to end: the step's inputs copied from pinned host memory, the graph
+    # replayed, the per-set counts read back, every step.
+    pts_h = pts.cpu().pin_memory()
+    offs_h = offs_d.cpu().pin_memory()
+    counts_h = torch.empty_like(counts, device="cpu").pin_memory()
+
+    def e2e_step():
+        pts.copy_(pts_h, non_blocking=True)
+        offs_d.copy_(offs_h, non_blocking=True)
+        step()
+        counts_h.copy_(counts, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_k = max(2, min(K, 5))
+    e2e_ms = max_over_ranks(time_steps(e2e_step, e2e_k, stream, dev), pg, dev)
+    e2e_same = bool(torch.equal(counts_h, ref_counts.cpu()))
 
     # The plain per-set form: one wg_upper_hood call per set, same GPU.
     lib = _lib.load()
@@ -330,14 +360,17 @@ def run_batched(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched {S} sets, sizes log-uniform in [3, 65536], mixed kinds",
                    "sets": S, "points": total, "corners": hsum, "seed": 5,
-                   "gpoints_per_s": total / (ms * 1e-3) / 1e9,
+                   "gpoints_per_s": total / (ms * 1e-3) / 1e9, "cuda_graph": True,
                    "l2": "input > 129 MB L2 (no flush)", "parallelism": f"replicas x{world}"},
         "compare": {"plain_per_set_ms_per_step": plain_ms, "plain_per_set_sets_per_s": S / (plain_ms * 1e-3),
-                    "batched_speedup": plain_ms / ms, "plain_counts_equal": same},
+                    "batched_speedup": plain_ms / ms, "plain_counts_equal": same,
+                    "direct_launch_ms_per_step": direct_ms, "graph_counts_equal": graph_same},
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_kind,
                      "kernel": "fused_kernel (batched)", "alg_bytes_per_launch": alg},
-        "e2e": {"value": None, "unit": "sets/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "e2e": {"value": S * world / (e2e_ms * 1e-3), "unit": "sets/s",
+                "h2d_bytes_per_step": 8 * total + 8 * (S + 1), "d2h_bytes_per_step": 4 * S,
+                "counts_equal": e2e_same},
         "gpu_launches": 2 * K,
         "clocks": clocks,
         "cpu_baseline": {"value": S / cpu_s, "unit": "sets/s", "cores": 1, "kind": "oracle",

@@ -191,8 +191,9 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx,
  * wg_debug_bridge: the bridge of two hoods P (hp corners) and Q (hq corners),
  *   P entirely left of Q, each a strictly convex upper chain: writes
  *   d_pq[0] = p, d_pq[1] = q with H(P u Q) = P[0..p] ++ Q[q..] (Section 2,
- *   mam 1-5). hp, hq >= 1. When hp, hq <= 32 the small-hood search (one
- *   corner per lane) runs as well; if it disagrees, d_pq = (-1, -1).
+ *   mam 1-5). hp, hq >= 1. The search that probes the end of P first runs
+ *   as well, and so does the small-hood search (one corner per lane) when
+ *   hp, hq <= 32; if either disagrees, d_pq = (-1, -1).
  * wg_debug_warp_hood: the hood of m <= 32 sorted distinct points computed by
  *   one warp in registers (stages d = 1..16 of the schedule); writes the
  *   corner positions to d_out[0..h) and h to d_out_count.

@@ -27,6 +27,11 @@ __global__ void dbg_bridge_kernel(const float2 *P, int hp, const float2 *Q, int 
 {
     PredCount pc;
     int2 pq = bridge_warp<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);
+    {
+        // the search that probes the end of P first must give the same bridge
+        const int2 r = bridge_tail<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);
+        if (r.x != pq.x || r.y != pq.y) pq = make_int2(-1, -1);
+    }
     if (hp <= 32 && hq <= 32) {
         // the small-hood search must give the same bridge
         const int2 r = bridge_small<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq);

@@ -170,11 +170,11 @@ __device__ __forceinline__ int tangent_from(PredCount &pc, float2 p, const QA &Q
 // sampling interval. Rounds: ceil(log32 hp); per lane ~log2(hq) + 1 tests.
 // Returns (p, q) in every lane.
 template <int MODE, class PA, class QA>
-__device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int hq)
+__device__ __noinline__ int2 bridge_warp_range(PredCount &pc, const PA &P, int lo, int hi, int thi, const QA &Q, int hq)
 {
+    // invariant: lo <= p* <= hi and !fLOW(hi); thi = tangent corner from
+    // P[hi] once a probe found it, else -1
     const int lane = lane_id();
-    int lo = 0, hi = hp - 1;  // invariant: lo <= p* <= hi and !fLOW(hi)
-    int thi = -1;             // tangent corner from P[hi], once a probe found it
     while (lo < hi) {
         const int span = hi - lo;
         const int step = (span + 31) >> 5;
@@ -201,6 +201,36 @@ __device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int
     }
     const int q = thi >= 0 ? thi : tangent_from<MODE>(pc, P.pt(lo), Q, hq);
     return make_int2(lo, q);
+}
+
+template <int MODE, class PA, class QA>
+__device__ int2 bridge_warp(PredCount &pc, const PA &P, int hp, const QA &Q, int hq)
+{
+    return bridge_warp_range<MODE>(pc, P, 0, hp - 1, -1, Q, hq);
+}
+
+// The same bridge when p* is expected near the end of P (a running hood
+// meeting the next chunk of points): the first round probes the last 32
+// candidates P[hp-33 .. hp-2] (one per lane). The f votes are LOW exactly
+// before p*, so a first non-LOW vote after the first probe fixes p*, no
+// non-LOW vote gives p* = hp - 1, and a non-LOW first probe leaves
+// p* <= hp - 33 to the sampled search.
+template <int MODE, class PA, class QA>
+__device__ int2 bridge_tail(PredCount &pc, const PA &P, int hp, const QA &Q, int hq)
+{
+    if (hp <= 33) return bridge_warp<MODE>(pc, P, hp, Q, hq);
+    const int lane = lane_id();
+    const int i0 = hp - 33;
+    const int i = i0 + lane;
+    const float2 p = P.pt(i);
+    const int t = tangent_from<MODE>(pc, p, Q, hq);
+    const bool low = orient<MODE>(pc, p, Q.pt(t), P.pt(i + 1)) > 0;
+    const unsigned nl = __ballot_sync(kFull, !low);
+    if (!nl) return make_int2(hp - 1, tangent_from<MODE>(pc, P.pt(hp - 1), Q, hq));
+    const int f = __ffs(nl) - 1;
+    const int tf = __shfl_sync(kFull, t, f);
+    if (f > 0) return make_int2(i0 + f, tf);
+    return bridge_warp_range<MODE>(pc, P, 0, i0, tf, Q, hq);
 }
 
 // The same bridge for small hoods (1 <= hp, hq <= 32), corners held one per

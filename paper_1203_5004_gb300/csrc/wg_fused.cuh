@@ -331,7 +331,7 @@ struct Warp {
             return;
         }
         const RunAcc ra{rxy(), R.g, R.gout, R.pts};
-        const int2 pq = bridge_warp<MODE>(pc, ra, R.g + R.w, PtrHood{hxy}, h);
+        const int2 pq = bridge_tail<MODE>(pc, ra, R.g + R.w, PtrHood{hxy}, h);
         if (pq.x < R.g) {
             R.g = pq.x + 1;
             R.w = 0;

@@ -92,7 +92,15 @@ def test_orient_small_differences_exact_without_fallback(wg):
 
 # ---------------------------------------------------------------- bridge
 def _hood_pair(r, n, span, kind):
-    if kind == "arc":
+    if kind == "concave":
+        # a strictly concave integer chain (every point a hood corner), some
+        # points pushed down: long hoods, bridges anywhere along them
+        i = np.arange(n, dtype=np.int64)
+        d = int(r.integers(1, 64))
+        kx = int(r.integers(0, inputs.G // 2)) + i * d
+        ky = (1 << 20) + i * (n - i) * int(r.integers(1, 8))
+        ky = ky - (r.random(n) < 0.2) * r.integers(0, 1 << 12, size=n)
+    elif kind == "arc":
         # points on the quantised parabola of the arc workload, in a narrow x
         # window: long runs of hood corners, near-collinear triples
         x0 = int(r.integers(0, inputs.G - (1 << 16)))
@@ -113,12 +121,12 @@ def _hood_pair(r, n, span, kind):
     return kx, ky, hp, hq
 
 
-@pytest.mark.parametrize("kind", ["fine", "coarse", "arc"])
+@pytest.mark.parametrize("kind", ["fine", "coarse", "arc", "concave"])
 def test_bridge_against_oracle(wg, kind):
-    r = np.random.default_rng({"fine": 2, "coarse": 3, "arc": 13}[kind])
+    r = np.random.default_rng({"fine": 2, "coarse": 3, "arc": 13, "concave": 14}[kind])
     checked = 0
     for trial in range(400):
-        n = int(r.integers(2, 3000 if kind != "arc" else 80))
+        n = int(r.integers(2, {"arc": 400, "concave": 600}.get(kind, 3000)))
         span = int(r.integers(2, 64)) if kind == "coarse" else inputs.G
         pair = _hood_pair(r, n, span, kind)
         if pair is None:
@@ -303,6 +311,56 @@ def test_batched(wg, num_sets, hi):
     for s in range(num_sets):
         a = offs[s]
         assert_same(out[a:a + cnt[s]], ref_out[a:a + ref_cnt[s]], f"set {s}")
+
+
+def test_cuda_graph_replay(wg):
+    # Both forms captured once in a CUDA graph and replayed: the workspace's
+    # counters (arrivals, call counter, batched queue) reset themselves, so
+    # every replay gives the oracle's corners.
+    ps = inputs.make("band", 1 << 20, 21)
+    ref = oracle.upper_hull(ps.kx, ps.ky)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    o = wg.default_options(tile_config=3)
+    wg.upper_hood_into(pts, out, cnt, ws, o)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        wg.upper_hood_into(pts, out, cnt, ws, o)
+    for _ in range(3):
+        out.fill_(-1)
+        cnt.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert_same(out[: int(cnt.item())].cpu().numpy(), ref, "single set, graph replay")
+    assert wg.device_status(ws) == 0
+
+    bps, offs, _ = inputs.batched(3000, seed=22)
+    bref_out, bref_cnt = oracle.upper_hull_batched(bps.kx, bps.ky, offs)
+    bpts = gpu_points(bps)
+    offs_d = torch.from_numpy(offs).to(DEV)
+    bout = torch.empty(max(int(offs[-1]), 1), dtype=torch.int32, device=DEV)
+    bcnt = torch.empty(len(offs) - 1, dtype=torch.int32, device=DEV)
+    bws = wg.new_workspace(wg.batched_workspace_size(offs))
+    wg.upper_hood_batched_into(bpts, offs_d, bout, bcnt, bws)
+    torch.cuda.synchronize()
+    bg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(bg):
+        wg.upper_hood_batched_into(bpts, offs_d, bout, bcnt, bws)
+    for _ in range(3):
+        bout.fill_(-1)
+        bcnt.fill_(-1)
+        bg.replay()
+        torch.cuda.synchronize()
+        c = bcnt.cpu().numpy()
+        assert_same(c, bref_cnt, "batched counts, graph replay")
+        o_ = bout.cpu().numpy()
+        for s_ in range(0, len(offs) - 1, 97):
+            a = int(offs[s_])
+            assert_same(o_[a:a + c[s_]], bref_out[a:a + bref_cnt[s_]], f"batched set {s_}, graph replay")
+    assert wg.device_status(bws) == 0
 
 
 @pytest.mark.slow
