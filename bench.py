@@ -51,13 +51,22 @@ WORKLOADS = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace collapsed."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the CUDA sources' code (comments and layout ignored), which
+    ties a committed ncu summary to the kernel it measured."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_5004_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -224,7 +224,7 @@ wg_status wg_debug_set_stall(void *workspace, int32_t stall_ns, wg_stream_t stre
  * allocator, or code that has nowhere to keep a workspace between calls.
  *
  * The caller passes only the input and the outputs (as for wg_upper_hood).
- * The bookkeeping lives in one fixed array (about 2.2 MB) in this library's
+ * The bookkeeping lives in one fixed array (about 3.3 MB) in this library's
  * own device memory, which every GPU that loads the library holds until the
  * process exits. It covers at most 2048 segments, and the call never plans
  * more, so every n from 0 to 2^31 - 1 fits; a larger n is rejected with

@@ -15,8 +15,12 @@
 //        already resident) is strictly higher; p then lies on or below a
 //        segment between two input points and cannot be a corner. A lane whose
 //        whole strip of K points is dropped this way learns it from the strip
-//        maximum alone (no per-point pass). A repeat of the previous input
-//        point is dropped too (first occurrence wins).
+//        maximum alone (no per-point pass). Where many strips survive (points
+//        along a sloped curve) the same test runs in the frame sheared by the
+//        tile's chord slope, with each height an interval that bounds its
+//        rounding. A repeat of the previous input point is dropped too (first
+//        occurrence wins), and so is a point with a strictly higher point
+//        directly above it and a point below it in its column or to its left;
 //      - a lane with survivors builds the hood of its strip serially (the
 //        paper's Section 3 strips);
 //      - surviving strip corners are appended, in order, to the warp's pending
@@ -27,13 +31,14 @@
 //    merged into the warp's running segment hood (a shared-memory window of
 //    its right end; older corners spill to the output array).
 //  * At the end of its segment a warp publishes the segment hood (indices in
-//    the output array, coordinates in the workspace), its count and the
-//    segment's maximum y. The warp that completes the last segment of a set
-//    (an atomic arrival count, no waiting) merges the segment hoods: a segment
-//    whose maximum is at most the maximum of all earlier segments and below
-//    that of some later segment is dropped whole (the same exact rule), and
-//    the corners of the remaining segments are streamed through the same tile
-//    pass.
+//    the output array; coordinates and indices staged in the workspace when
+//    they fit one window), its count and the segment's maximum y. The second
+//    of two neighbouring segments to be published bridges the pair. The CTA
+//    whose warp completes the last segment of a set (an atomic arrival count,
+//    no waiting) merges the segment hoods: a staircase of the segment maxima
+//    drops whole segments (the same exact rule), then the bridges of the
+//    remaining neighbours, dropping hoods that contribute nothing, and the
+//    kept ranges are copied to the output.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
