@@ -253,6 +253,46 @@ def test_configs(wg, name, make):
     assert_same(got, ref, name)
 
 
+_FULL = {}
+
+
+def _full(name):
+    # the bench's full-size workloads, each generated and solved by the
+    # oracle once per test session
+    if name not in _FULL:
+        ps = {"uniform26": lambda: inputs.uniform(1 << 26, 7), "band26": lambda: inputs.band(1 << 26, 4),
+              "arc24": lambda: inputs.arc(1 << 24, 3)}[name]()
+        _FULL[name] = (ps, oracle.upper_hull(ps.kx, ps.ky))
+    return _FULL[name]
+
+
+@pytest.mark.parametrize("name", ["uniform26", "band26", "arc24"])
+@pytest.mark.parametrize("cfg,spc", [(1, 1), (2, 1), (2, 2), (3, 1), (3, 2), (4, 1)])
+def test_full_size_every_launch_configuration(wg, name, cfg, spc):
+    # every tile configuration and segment count the autotuner may pick for
+    # the bench's workloads, at their full sizes
+    ps, ref = _full(name)
+    got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(tile_config=cfg, segments_per_cta=spc))
+    assert_same(got.cpu().numpy(), ref, f"{name} cfg{cfg} spc{spc}")
+
+
+@pytest.mark.parametrize("name", ["uniform26", "band26"])
+def test_full_size_autotuned_as_benched(wg, name):
+    # the launch bench.py times: the autotuner's choice, then calls on one
+    # workspace back to back
+    ps, ref = _full(name)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    best = wg.autotune(pts, ws)
+    out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    for _ in range(3):
+        wg.upper_hood_into(pts, out, cnt, ws, best)
+    torch.cuda.synchronize()
+    assert_same(out[: int(cnt.item())].cpu().numpy(), ref, f"{name} autotuned")
+    assert wg.device_status(ws) == 0
+
+
 def test_band_2_26_filtered_and_fp64(wg):
     ps = inputs.band(1 << 26, 4)
     ref = oracle.upper_hull(ps.kx, ps.ky)
