@@ -35,8 +35,11 @@
  *     wait that gave up, invalid input in validation mode) are recorded in a
  *     status word inside the workspace; read it with wg_get_device_status.
  *   - A workspace must be zero-filled once before its first use (cudaMemset);
- *     every call leaves it ready for the next. Calls that share one workspace
- *     must not overlap on the GPU (use one stream, or one workspace each).
+ *     every call leaves it ready for the next, and replays of a captured
+ *     CUDA graph are calls like any other. After a call that recorded a
+ *     device error (wg_get_device_status != WG_OK), zero-fill it again.
+ *     Calls that share one workspace must not overlap on the GPU (use one
+ *     stream, or one workspace each).
  */
 #ifndef WG_H_
 #define WG_H_
