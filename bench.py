@@ -58,13 +58,18 @@ def _code_only(text: str) -> str:
     return " ".join(text.split())
 
 
+# The sources that define the fused kernel (device code and its instantiations).
+KERNEL_SOURCES = ("wg_device.cuh", "wg_fused.cuh", "wg_internal.h", "wg_fused.cu", "wg_fused_cfg1.cu",
+                  "wg_fused_cfg2.cu", "wg_fused_cfg3.cu", "wg_fused_cfg4.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources' code (comments and layout ignored), which
-    ties a committed ncu summary to the kernel it measured."""
+    """Hash of the fused kernel's sources (code only: comments and layout
+    ignored), which ties a committed ncu summary to the kernel it measured."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_5004_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in KERNEL_SOURCES:
             with open(os.path.join(csrc, name), encoding="utf-8") as f:
                 h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]

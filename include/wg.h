@@ -78,7 +78,8 @@ typedef struct wg_options {
     int32_t pred_mode;       /* wg_pred_mode */
     int32_t count_predicates;/* 1: count orientation tests and float64 fallbacks (slower) */
     int32_t validate;        /* 1: check grid membership and order; report WG_ERR_* on device */
-    int32_t tile_config;     /* 0 = library choice (autotuned if wg_autotune ran); else 1..WG_NUM_TILE_CONFIGS */
+    int32_t tile_config;     /* 0 = library choice (single set: autotuned if wg_autotune ran, else 1;
+                                batched: 3); else 1..WG_NUM_TILE_CONFIGS */
     int32_t segments_per_cta;/* 0 = library choice; else segments per resident CTA (1..8) */
     int32_t reserved[3];
 } wg_options;

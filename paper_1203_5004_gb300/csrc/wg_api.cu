@@ -48,7 +48,8 @@ constexpr size_t kOffSegSidx = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
 constexpr size_t kOffSegPair = kOffSegSidx + 4 * (size_t)kStageCorners * kMaxSeg;
 constexpr size_t kOffSegBridge = kOffSegPair + 4 * (size_t)kMaxSeg;
 constexpr size_t kSingleWsBytes = kOffSegBridge + 8 * (size_t)kMaxSeg;
-constexpr int kDefaultCfg = 1;
+constexpr int kDefaultCfg = 1;         // single set, before any autotuning (best for small n)
+constexpr int kBatchedDefaultCfg = 3;  // batched form (measured best on the mixed 100k-set workload)
 
 struct DevInfo {
     bool init = false;
@@ -347,7 +348,7 @@ wg_status wg_upper_hood_batched(const float *points, const int64_t *offsets, int
     st = dev_info(&d);
     if (st != WG_OK) return st;
     if (num_sets == 0) return WG_OK;
-    const int cfg = o.tile_config ? o.tile_config : kDefaultCfg;
+    const int cfg = o.tile_config ? o.tile_config : kBatchedDefaultCfg;
     const cudaError_t e = batched_launch(points, offsets, num_sets, out_idx, out_counts, workspace,
                                          ws_bytes, cfg, pred_mode_bits(o), o.validate, S(stream));
     if (e == cudaErrorInvalidValue) return WG_ERR_WORKSPACE;
