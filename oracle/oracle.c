@@ -18,7 +18,7 @@
  * in int64: differences are below 2^24 in magnitude, products below 2^48 and
  * the determinant below 2^49.
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *  - order is lexicographic (x, y), so equal x values are allowed;
  *  - a point equal to an earlier point is never a corner (first occurrence
  *    wins);
