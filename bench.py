@@ -41,7 +41,7 @@ METRIC = "upper-hull Gpoints/s and % HBM roofline; batched sets/s vs plain per-s
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {
-    "uniform26": ("uniform", 1 << 26, 7, "uniform n=2^26 single set (north-star target)"),
+    "uniform26": ("uniform", 1 << 26, 7, "uniform n=2^26 single set"),
     "uniform24": ("uniform", 1 << 24, 2, "uniform n=2^24 single set"),
     "arc24": ("arc", 1 << 24, 3, "arc y=1-4(x-1/2)^2 n=2^24 single set"),
     "band26": ("band", 1 << 26, 4, "parabola band 2^-20 wide n=2^26 single set"),
