@@ -83,6 +83,21 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def profiled_traffic_per_point(workload: str):
+    """dram bytes per input point from a committed ncu summary of a smaller
+    case of the same workload, if it matches this kernel."""
+    path = os.path.join(ROOT, "profiles", f"fused_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_point:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
 def profiled_traffic(workload: str):
     """dram bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", f"fused_{workload}.md")
@@ -299,6 +314,11 @@ def run_batched(args, world, rank, local):
     for _ in range(max(3, args.warmup)):
         direct()
     torch.cuda.synchronize(dev)
+    if args.profile:
+        for _ in range(args.steps):
+            direct()
+        torch.cuda.synchronize(dev)
+        return
     ref_counts = counts.clone()
     # One step (planning kernel + persistent fused kernel) captured in a CUDA
     # graph; the workspace's counters reset themselves, so replays are exact.
@@ -386,6 +406,8 @@ def run_batched(args, world, rank, local):
     cpu_s = time.perf_counter() - t0
     peak, peak_kind = measured_peak()
     alg = 8 * total + 4 * hsum + 8 * (S + 1) + 4 * S
+    per_point = profiled_traffic_per_point("batched")
+    traffic = per_point * total if per_point is not None else None
     line = {
         "metric": METRIC, "value": value, "unit": "sets/s", "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -398,7 +420,7 @@ def run_batched(args, world, rank, local):
                     "batched_speedup": plain_ms / ms, "plain_counts_equal": same,
                     "direct_launch_ms_per_step": direct_ms, "graph_counts_equal": graph_same},
         "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": traffic, "peak_source": peak_kind,
                      "kernel": "fused_kernel (batched)", "alg_bytes_per_launch": alg},
         "e2e": {"value": S * world / (e2e_ms * 1e-3), "unit": "sets/s",
                 "h2d_bytes_per_step": 8 * total + 8 * (S + 1), "d2h_bytes_per_step": 4 * S,
