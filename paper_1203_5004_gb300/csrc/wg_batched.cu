@@ -57,7 +57,7 @@ static BatchLayout batch_layout(int num_sets, long long max_items, long long max
     o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 4);
     L.stage_bridge = o;
     o = align256(o + (size_t)std::max<long long>(max_stage, 1) * 8);
-    L.ctl = o;  // num_items, queue, done, bounds
+    L.ctl = o;  // items, queue, done, items per bin, bin cursors, stage cursor
     o = align256(o + 64);
     L.total = o;
     L.max_items = max_items;
@@ -88,53 +88,91 @@ size_t batched_workspace_bytes(const int64_t *h_offsets, int num_sets)
 
 __device__ __forceinline__ int bin_of(long long tiles) { return tiles >= 8 ? 0 : (tiles >= 2 ? 1 : 2); }
 
+// Segments of a set of n points: one per kMaxTilesPerSeg tiles (at most
+// kMaxSegPerSet), and its size bin.
+__device__ __forceinline__ int set_segments(long long n, int T, int &bin)
+{
+    const long long tiles = (n + T - 1) / T;
+    bin = bin_of(tiles);
+    return (int)min((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, (long long)kMaxSegPerSet);
+}
+
+// Planning, in two grid-wide passes. ctl: [0] items, [1] queue, [2] done,
+// [3..5] items per bin, [6..8] bin cursors, [9] stage-slot cursor (3..9
+// cleared before the first pass).
+// Pass 1: items per size bin (one global add per bin and block).
 __global__ void __launch_bounds__(kPlanThreads)
-    batch_plan_kernel(const int64_t *off, int num_sets, int T, SegItem *items, long long max_items,
-                      long long max_stage, int *ctl, int32_t *out_counts, int *status)
+    batch_count_kernel(const int64_t *off, int num_sets, int T, int *ctl, int32_t *out_counts)
 {
     __shared__ int s_bin[kBins];
-    __shared__ int s_cur[kBins];
-    __shared__ int s_stage;
     const int tid = threadIdx.x;
     if (tid < kBins) s_bin[tid] = 0;
-    if (tid == 0) s_stage = 0;
     __syncthreads();
-    for (int s = tid; s < num_sets; s += kPlanThreads) {
+    for (int s = blockIdx.x * kPlanThreads + tid; s < num_sets; s += gridDim.x * kPlanThreads) {
         const long long n = off[s + 1] - off[s];
         if (n <= 0) {
             out_counts[s] = 0;
             continue;
         }
-        const long long tiles = (n + T - 1) / T;
-        const int nseg = (int)min((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, (long long)kMaxSegPerSet);
-        atomicAdd(&s_bin[bin_of(tiles)], nseg);
+        int bin;
+        const int nseg = set_segments(n, T, bin);
+        atomicAdd(&s_bin[bin], nseg);
     }
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int b = 0; b < kBins; ++b) {
-            s_cur[b] = acc;
-            acc += s_bin[b];
-        }
-        if (acc > max_items) {
-            atomicCAS(status, 0, 2);
-            acc = 0;
-        }
-        ctl[0] = acc;  // number of items
-        ctl[1] = 0;    // queue
-        ctl[2] = 0;    // done
+    if (tid < kBins && s_bin[tid]) atomicAdd(ctl + 3 + tid, s_bin[tid]);
+}
+
+// Pass 2: every set's items, written at its bin's offset (larger sets
+// first), with stage slots for sets of several segments. A block reserves
+// its ranges with one global add per bin, then places its own sets.
+__global__ void __launch_bounds__(kPlanThreads)
+    batch_assign_kernel(const int64_t *off, int num_sets, int T, SegItem *items, long long max_items,
+                        long long max_stage, int *ctl, int *status)
+{
+    __shared__ int s_bin[kBins];
+    __shared__ int s_cur[kBins];
+    __shared__ int s_stage, s_stage_cur;
+    const int tid = threadIdx.x;
+    int base[kBins];
+    long long acc = 0;
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        base[b] = (int)acc;
+        acc += ctl[3 + b];
+    }
+    const bool over = acc > max_items;
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl[0] = over ? 0 : (int)acc;  // number of items
+        ctl[1] = 0;                    // queue
+        ctl[2] = 0;                    // done
+        if (over) atomicCAS(status, 0, 2);
+    }
+    if (over || acc == 0) return;
+    if (tid < kBins) s_bin[tid] = 0;
+    if (tid == 0) s_stage = 0;
+    __syncthreads();
+    for (int s = blockIdx.x * kPlanThreads + tid; s < num_sets; s += gridDim.x * kPlanThreads) {
+        const long long n = off[s + 1] - off[s];
+        if (n <= 0) continue;
+        int bin;
+        const int nseg = set_segments(n, T, bin);
+        atomicAdd(&s_bin[bin], nseg);
+        if (nseg > 1) atomicAdd(&s_stage, nseg);
     }
     __syncthreads();
-    if (ctl[0] == 0) return;
-    for (int s = tid; s < num_sets; s += kPlanThreads) {
+    if (tid < kBins) s_cur[tid] = base[tid] + (s_bin[tid] ? atomicAdd(ctl + 6 + tid, s_bin[tid]) : 0);
+    if (tid == 0) s_stage_cur = s_stage ? atomicAdd(ctl + 9, s_stage) : 0;
+    __syncthreads();
+    for (int s = blockIdx.x * kPlanThreads + tid; s < num_sets; s += gridDim.x * kPlanThreads) {
         const long long a0 = off[s], n = off[s + 1] - a0;
         if (n <= 0) continue;
+        int bin;
+        const int nseg = set_segments(n, T, bin);
         const long long tiles = (n + T - 1) / T;
-        const int nseg = (int)min((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, (long long)kMaxSegPerSet);
-        const int base = atomicAdd(&s_cur[bin_of(tiles)], nseg);
+        const int slot0 = atomicAdd(&s_cur[bin], nseg);
         int stage = 0;
         if (nseg > 1) {
-            stage = atomicAdd(&s_stage, nseg);
+            stage = atomicAdd(&s_stage_cur, nseg);
             if (stage + nseg > max_stage) {
                 atomicCAS(status, 0, 2);
                 stage = 0;
@@ -149,10 +187,10 @@ __global__ void __launch_bounds__(kPlanThreads)
             it.set = s;
             it.c = c;
             it.nseg = nseg;
-            it.slot = base + c;
-            it.slot0 = base;
+            it.slot = slot0 + c;
+            it.slot0 = slot0;
             it.pad = stage + c;
-            items[base + c] = it;
+            items[slot0 + c] = it;
         }
     }
 }
@@ -176,16 +214,21 @@ cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_
     int *ctl = reinterpret_cast<int *>(w + L.ctl);
     SegItem *items = reinterpret_cast<SegItem *>(w + L.items);
     const int T = fused_tile_points(cfg);
-    batch_plan_kernel<<<1, kPlanThreads, 0, st>>>(offsets, num_sets, T, items, L.max_items, L.max_stage, ctl,
-                                                  out_counts, &hdr->status);
-    cudaError_t e = cudaGetLastError();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int plan_blocks =
+        (int)std::max(1LL, std::min<long long>((num_sets + kPlanThreads - 1) / kPlanThreads, 4LL * std::max(1, sms)));
+    cudaError_t e = cudaMemsetAsync(ctl + 3, 0, 7 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    batch_count_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, ctl, out_counts);
+    batch_assign_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, items, L.max_items,
+                                                              L.max_stage, ctl, &hdr->status);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
 
     int blocks = 0;
     if ((e = fused_occupancy(cfg, &blocks)) != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     FusedArgs a;
     std::memset(&a, 0, sizeof(a));
     a.points = points;
