@@ -320,7 +320,7 @@ def run_batched(args, world, rank, local):
         torch.cuda.synchronize(dev)
         return
     ref_counts = counts.clone()
-    # One step (planning kernel + persistent fused kernel) captured in a CUDA
+    # One step (two planning kernels + the persistent fused kernel) captured in a CUDA
     # graph; the workspace's counters reset themselves, so replays are exact.
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
@@ -425,7 +425,7 @@ def run_batched(args, world, rank, local):
         "e2e": {"value": S * world / (e2e_ms * 1e-3), "unit": "sets/s",
                 "h2d_bytes_per_step": 8 * total + 8 * (S + 1), "d2h_bytes_per_step": 4 * S,
                 "counts_equal": e2e_same},
-        "gpu_launches": 2 * K,
+        "gpu_launches": 3 * K,
         "clocks": clocks,
         "cpu_baseline": {"value": S / cpu_s, "unit": "sets/s", "cores": 1, "kind": "oracle",
                          "sample": f"all {S} sets once, single-thread monotone chain, {cpu_s:.1f} s"},
