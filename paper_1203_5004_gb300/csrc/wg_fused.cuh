@@ -842,9 +842,10 @@ struct Warp {
     }
 
     // End of a segment of a multi-segment set: publish the segment hood (its
-    // indices are already in the output array; its coordinates go to the
-    // workspace when it fits one window), its count and its max y. `last` is
-    // set in the warp that completed the set's last segment.
+    // indices are already in the output array; its coordinates and indices
+    // are also staged in the workspace when it fits one window), its count
+    // and its max y. `last` is set in the warp that completed the set's last
+    // segment.
     __device__ void publish(const SegItem &it, int item_index, RState &R, float segmax, bool &last)
     {
         const SegStore ss = store();
