@@ -80,11 +80,17 @@ typedef struct wg_options {
     int32_t validate;        /* 1: check grid membership and order; report WG_ERR_* on device */
     int32_t tile_config;     /* 0 = library choice (single set: autotuned if wg_autotune ran, else 1;
                                 batched: 3); else 1..WG_NUM_TILE_CONFIGS */
-    int32_t segments_per_cta;/* 0 = library choice; else segments per resident CTA (1..8) */
-    int32_t reserved[3];
+    int32_t segments_per_cta;/* 0 = library choice; else the schedule plans its first, long segments
+                                for this many times the resident warps (1..8) */
+    int32_t schedule;        /* single set: 0 = library choice; 1 = balanced (one segment per warp,
+                                equal shares); 2 = guided (long segments first, then shorter ones
+                                claimed by warps as they become free) */
+    int32_t reserved[2];
 } wg_options;
 
 #define WG_NUM_TILE_CONFIGS 4
+#define WG_SCHEDULE_BALANCED 1
+#define WG_SCHEDULE_GUIDED 2
 
 /* Fills *opts with the defaults (filtered predicate, no counters, no
  * validation, library-chosen tiling). */

@@ -6,8 +6,10 @@ product path never does: the CUDA library fails loudly instead of falling back
 here.
 
 ``oracle.c`` holds the arithmetic (Andrew's monotone chain and an O(n^3) brute
-force, both with exact int64 orientation). This module only compiles it with
-gcc, loads it with ctypes and marshals numpy arrays.
+force, both with exact int64 orientation). ``strips.c`` runs the same chain on
+contiguous strips in parallel threads and once more over the strip hoods (the
+CPU baseline of the measurements). This module only compiles them with gcc,
+loads them with ctypes and marshals numpy arrays.
 
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 (brute force, closed forms, Qhull in general position, invariants, Python
@@ -24,16 +26,17 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "strips.c"))
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, -O2, no -march)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle sources into liboracle.so next to them (gcc, -O2, no -march)."""
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-pthread", "-shared", "-fPIC", "-o", tmp, *_SRCS])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -48,6 +51,8 @@ def _load():
             i8p = ctypes.POINTER(ctypes.c_int8)
             lib.oracle_upper_hull.restype = ctypes.c_int64
             lib.oracle_upper_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_upper_hull_strips.restype = ctypes.c_int64
+            lib.oracle_upper_hull_strips.argtypes = [i32p, i32p, ctypes.c_int64, i32p, ctypes.c_int]
             lib.oracle_upper_hull_brute.restype = ctypes.c_int64
             lib.oracle_upper_hull_brute.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
             lib.oracle_orient_sign.restype = ctypes.c_int
@@ -78,6 +83,18 @@ def upper_hull(kx, ky) -> np.ndarray:
     out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
     h = _load().oracle_upper_hull(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
                                   kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def upper_hull_strips(kx, ky, threads: int | None = None) -> np.ndarray:
+    """The same corners by the strip-parallel chain on `threads` host threads (default: all cores)."""
+    kx, ky = _ints(kx, ky)
+    t = int(threads) if threads else (os.cpu_count() or 1)
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    h = _load().oracle_upper_hull_strips(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                         kx.shape[0], _p(out, ctypes.c_int32), t)
+    if h < 0:
+        raise MemoryError("oracle_upper_hull_strips: out of memory or threads")
     return out[:h].copy()
 
 

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
         ("validate", _i32),
         ("tile_config", _i32),
         ("segments_per_cta", _i32),
-        ("reserved", _i32 * 3),
+        ("schedule", _i32),
+        ("reserved", _i32 * 2),
     ]
 
 

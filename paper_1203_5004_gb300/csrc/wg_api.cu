@@ -37,8 +37,9 @@ namespace {
 
 // Single-set workspace: header | arrivals | per segment: count, max y,
 // final-merge scratch (16 ints), staged hood coordinates and indices
-// (kStageCorners), pair word and pair bridge.
-constexpr int kMaxSeg = 4096;        // segments (warp streams) of one fused call
+// (kStageCorners), pair word, pair bridge, hood list, list bridges (two
+// ints) and output plan (four ints).
+constexpr int kMaxSeg = kMaxSegSingle;  // segments of one fused call
 constexpr size_t kOffArrivals = 256;
 constexpr size_t kOffSegCount = 512;
 constexpr size_t kOffSegYmax = kOffSegCount + 4 * kMaxSeg;
@@ -47,7 +48,11 @@ constexpr size_t kOffSegXy = kOffSegLive + 64 * kMaxSeg;
 constexpr size_t kOffSegSidx = kOffSegXy + 8 * (size_t)kStageCorners * kMaxSeg;
 constexpr size_t kOffSegPair = kOffSegSidx + 4 * (size_t)kStageCorners * kMaxSeg;
 constexpr size_t kOffSegBridge = kOffSegPair + 4 * (size_t)kMaxSeg;
-constexpr size_t kSingleWsBytes = kOffSegBridge + 8 * (size_t)kMaxSeg;
+constexpr size_t kOffListLid = kOffSegBridge + 8 * (size_t)kMaxSeg;
+constexpr size_t kOffListBp = kOffListLid + 4 * (size_t)kMaxSeg;
+constexpr size_t kOffListBq = kOffListBp + 4 * (size_t)kMaxSeg;
+constexpr size_t kOffPlan = kOffListBq + 4 * (size_t)kMaxSeg;
+constexpr size_t kSingleWsBytes = kOffPlan + 16 * (size_t)kMaxSeg;
 constexpr int kDefaultCfg = 1;         // single set, before any autotuning (best for small n)
 constexpr int kBatchedDefaultCfg = 3;  // batched form (measured best on the mixed 100k-set workload)
 
@@ -65,6 +70,7 @@ DevInfo g_dev[64];
 struct Tuned {
     int cfg = 0;
     int spc = 0;
+    int sched = 0;
 };
 Tuned g_tuned[64][33];
 
@@ -129,6 +135,7 @@ wg_status check_opts(const wg_options &o)
     if (o.pred_mode != WG_PRED_FILTERED && o.pred_mode != WG_PRED_FP64) return WG_ERR_INVALID_VALUE;
     if (o.tile_config < 0 || o.tile_config > kNumTileCfgs) return WG_ERR_INVALID_VALUE;
     if (o.segments_per_cta < 0 || o.segments_per_cta > 8) return WG_ERR_INVALID_VALUE;
+    if (o.schedule < 0 || o.schedule > WG_SCHEDULE_GUIDED) return WG_ERR_INVALID_VALUE;
     return WG_OK;
 }
 
@@ -183,23 +190,23 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
 
     int dev = 0;
     cudaGetDevice(&dev);
-    int cfg = o.tile_config, spc = o.segments_per_cta;
+    int cfg = o.tile_config, spc = o.segments_per_cta, sched = o.schedule;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         const Tuned &t = g_tuned[dev][bucket(n)];
         if (cfg == 0) cfg = t.cfg ? t.cfg : kDefaultCfg;
         if (spc == 0) spc = t.spc ? t.spc : 1;
+        if (sched == 0) sched = t.sched ? t.sched : WG_SCHEDULE_GUIDED;
     }
-    // One segment of whole tiles per warp stream; segments_per_cta > 1 only
-    // shortens segments (more CTAs than fit at once), it never gives a warp
-    // two segments.
+    // Segments are claimed dynamically by the warps of one resident wave of
+    // CTAs; segments_per_cta scales the number of warps the schedule plans
+    // its first, long segments for (more, shorter segments when > 1).
     const int T = fused_tile_points(cfg);
     const int W = fused_warps(cfg);
     const long long tiles = (n + T - 1) / T;
     const int resident = std::max(1, d->occ[cfg]) * d->sms;
-    long long nseg = std::min<long long>(tiles, (long long)resident * W * spc);
-    nseg = std::min<long long>(nseg, kMaxSeg);
-    const int grid = (int)((nseg + W - 1) / W);
+    const Schedule sch = make_schedule(tiles, (long long)resident * W * spc, kMaxSeg, sched == WG_SCHEDULE_BALANCED);
+    const int grid = (int)std::min<long long>(resident, (sch.nseg + W - 1) / W);
 
     FusedArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -208,7 +215,11 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     a.out_count = out_count;
     a.n = n;
     a.tiles = (int)tiles;
-    a.nseg = (int)nseg;
+    a.nseg = sch.nseg;
+    a.sch_n1 = sch.n1;
+    a.sch_l1 = sch.l1;
+    a.sch_n2 = sch.n2;
+    a.sch_l2 = sch.l2;
     a.items = nullptr;
     a.validate = o.validate ? 1 : 0;
     a.hdr = reinterpret_cast<WsHeader *>(workspace);
@@ -220,6 +231,10 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     a.seg_sidx = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffSegSidx);
     a.seg_pair = reinterpret_cast<unsigned *>(static_cast<char *>(workspace) + kOffSegPair);
     a.seg_bridge = reinterpret_cast<unsigned long long *>(static_cast<char *>(workspace) + kOffSegBridge);
+    a.list_lid = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffListLid);
+    a.list_bp = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffListBp);
+    a.list_bq = reinterpret_cast<int *>(static_cast<char *>(workspace) + kOffListBq);
+    a.plan = reinterpret_cast<int4 *>(static_cast<char *>(workspace) + kOffPlan);
     if (fused_launch(cfg, a, grid, pred_mode_bits(o), S(stream)) != cudaSuccess) return WG_ERR_CUDA;
     return WG_OK;
 }
@@ -432,12 +447,14 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WG_ERR_CUDA;
     float best_ms = 1e30f;
-    int best_cfg = kDefaultCfg, best_spc = 1;
-    const int spcs[] = {1, 2, 4};
+    int best_cfg = kDefaultCfg, best_spc = 1, best_sched = WG_SCHEDULE_GUIDED;
+    const int variants[][2] = {{WG_SCHEDULE_BALANCED, 1}, {WG_SCHEDULE_GUIDED, 1}, {WG_SCHEDULE_GUIDED, 2}};
     for (int cfg = 1; cfg <= kNumTileCfgs; ++cfg) {
-        for (int spc : spcs) {
+        for (const auto &var : variants) {
+            const int spc = var[1];
             o.tile_config = cfg;
             o.segments_per_cta = spc;
+            o.schedule = var[0];
             if ((st = wg_upper_hood_ex(points, n, out_idx, out_count, workspace, ws_bytes, &o, stream)) != WG_OK)
                 break;
             const int reps = 5;
@@ -456,6 +473,7 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
                 best_ms = ms;
                 best_cfg = cfg;
                 best_spc = spc;
+                best_sched = var[0];
             }
         }
         if (st != WG_OK) break;
@@ -465,11 +483,12 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
     if (st != WG_OK) return st;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        g_tuned[dev][bucket(n)] = Tuned{best_cfg, best_spc};
+        g_tuned[dev][bucket(n)] = Tuned{best_cfg, best_spc, best_sched};
     }
     wg_options_default(best);
     best->tile_config = best_cfg;
     best->segments_per_cta = best_spc;
+    best->schedule = best_sched;
     return WG_OK;
 }
 

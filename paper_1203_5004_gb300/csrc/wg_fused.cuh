@@ -51,7 +51,8 @@ namespace wg {
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s bound on any device wait
 __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
 
-constexpr int kShearLanes = 3;  // more surviving strips than this: shear the tile
+constexpr int kShearLanes = 3;         // more surviving strips than this: shear the tile
+constexpr int kShearBackoffLanes = 8;  // after failed trials, skip trials only up to this many
 
 // The frame in which a tile's points are compared by height: y itself, or
 // the sheared y' = (y - y0) - s (x - x0). Shearing keeps every orientation.
@@ -77,26 +78,31 @@ struct Frame {
 // inside a strip each point is tested the same way. The frame is kept only if
 // fewer strips survive than the plain test's `live_plain`. Returns the lane's
 // mask of remaining points in the low 32 bits and 1 in bit 32 when the frame
-// is kept (warp-uniform), 0 otherwise. Not inlined: it runs on few tiles and
-// stays out of the hot loop's code.
+// is kept (warp-uniform), 0 otherwise. The strip's bounds are computed once
+// and kept in registers for the three passes. Any slope gives an exact test
+// (the bounds cover the roundings for the slope actually used), so the chord
+// slope is taken from a fast division.
 template <int K>
-__device__ __noinline__ unsigned long long sheared_tile(const float2 *tb, int cnt, int nvalid, int live_plain,
-                                                       float2 prev_pt, bool has_prev)
+__device__ __forceinline__ unsigned long long sheared_tile(const float2 *tb, int cnt, int nvalid, int live_plain,
+                                                          float2 prev_pt, bool has_prev)
 {
     const int lane = threadIdx.x & 31;
     const int sbase = lane * K;
     const float2 f0 = tb[0], f1 = tb[cnt - 1];
-    float sl = f1.x > f0.x ? (f1.y - f0.y) / (f1.x - f0.x) : 0.f;
+    float sl = f1.x > f0.x ? __fdividef(f1.y - f0.y, f1.x - f0.x) : 0.f;
     if (!(fabsf(sl) < 1e6f)) sl = 0.f;
     const Frame f{f0.x, f0.y, sl, sl != 0.f ? 0x1p-22f : 0.f};
-    const int m = min(K, nvalid);
+    float lo[K], hi[K];
     float mlo = neg_inf(), mhi = neg_inf();
-#pragma unroll 1
-    for (int j = 0; j < m; ++j) {
-        float l, h;
-        f.bounds(tb[sbase + j], l, h);
-        mlo = fmaxf(mlo, l);
-        mhi = fmaxf(mhi, h);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        lo[j] = neg_inf();
+        hi[j] = neg_inf();
+        if (j < nvalid) {
+            f.bounds(tb[sbase + j], lo[j], hi[j]);
+            mlo = fmaxf(mlo, lo[j]);
+            mhi = fmaxf(mhi, hi[j]);
+        }
     }
     float carry = neg_inf();
     if (has_prev) {
@@ -117,21 +123,18 @@ __device__ __noinline__ unsigned long long sheared_tile(const float2 *tb, int cn
     if (!dead && nvalid > 0) {
         unsigned kpre = 0;
         float pm = pm0;
-#pragma unroll 1
-        for (int j = 0; j < m; ++j) {
-            float lo, hi;
-            f.bounds(tb[sbase + j], lo, hi);
-            kpre |= (hi <= pm ? 1u : 0u) << j;
-            pm = fmaxf(pm, lo);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            kpre |= (hi[j] <= pm ? 1u : 0u) << j;
+            pm = fmaxf(pm, lo[j]);
         }
         float smx = suf;
-#pragma unroll 1
-        for (int j = m - 1; j >= 0; --j) {
-            float lo, hi;
-            f.bounds(tb[sbase + j], lo, hi);
-            if (!(((kpre >> j) & 1u) && hi < smx)) surv |= 1u << j;
-            smx = fmaxf(smx, lo);
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j) {
+            if (!(((kpre >> j) & 1u) && hi[j] < smx)) surv |= 1u << j;
+            smx = fmaxf(smx, lo[j]);
         }
+        surv &= nvalid >= K ? (K == 32 ? kFull : ((1u << K) - 1u)) : ((1u << nvalid) - 1u);
     }
     return (1ull << 32) | surv;
 }
@@ -148,14 +151,14 @@ struct Cfg {
     static constexpr size_t kOffPidx = kOffPxy + size_t(PCAP) * 8;
     static constexpr size_t kOffRxy = kOffPidx + size_t(PCAP) * 4;
     static constexpr size_t kOffRidx = kOffRxy + size_t(RCAP) * 8;
-    static constexpr size_t kOffDesc = kOffRidx + size_t(RCAP) * 4;
-    static constexpr size_t kOffBar = kOffDesc + size_t(PCAP / 32) * 8;
+    static constexpr size_t kOffMeta = kOffRidx + size_t(RCAP) * 4;  // per ring slot: tile start, count, flags
+    static constexpr size_t kOffBar = kOffMeta + size_t(S) * 16;
     static constexpr size_t kWarpBytes = ((kOffBar + 8 * (S + 1)) + 127) / 128 * 128;
     // after the warp regions: one CTA word (the item whose merge this CTA runs)
     static constexpr size_t kBytes = kWarpBytes * W + 128;
     static_assert(K % 2 == 1 && K < 32, "K must be odd (bank-conflict-free strips) and < 32");
     static_assert(S >= 3, "three tile buffers: current, look-ahead, in flight");
-    static_assert(RCAP % 64 == 0 && PCAP % 32 == 0 && PCAP >= 64, "window / list sizes");
+    static_assert(RCAP % 64 == 0 && PCAP % 32 == 0 && PCAP >= 64 && PCAP <= 256, "window / list sizes");
     static_assert(kT % 2 == 0, "even tile");
     static_assert(RCAP == kStageCorners, "staged segment hoods hold one window");
 };
@@ -205,7 +208,6 @@ struct Warp {
     float xfirst;         // x of the set's first point (column rule)
     int sh_skip, sh_fail;  // sheared-frame trials: tiles to skip, failures in a row
     unsigned tag;          // this call's tag (pair words, pair bridges)
-    int pp_item, pp_count; // single set: the segment whose pair bridges wait for the CTA (-1: none)
 
     __device__ Warp(const FusedArgs &a, unsigned char *b) : args(a), base(b), pn(0) { lane = threadIdx.x & 31; }
 
@@ -214,19 +216,17 @@ struct Warp {
     __device__ int *pidx() const { return reinterpret_cast<int *>(base + C::kOffPidx); }
     __device__ float2 *rxy() const { return reinterpret_cast<float2 *>(base + C::kOffRxy); }
     __device__ int *ridx() const { return reinterpret_cast<int *>(base + C::kOffRidx); }
-    __device__ int2 *desc() const { return reinterpret_cast<int2 *>(base + C::kOffDesc); }
     __device__ uint64_t *bars() const { return reinterpret_cast<uint64_t *>(base + C::kOffBar); }
+    __device__ int4 *meta() const { return reinterpret_cast<int4 *>(base + C::kOffMeta); }
 
     // ------------------------------------------------------------------ items
     __device__ SegItem item(int i) const
     {
         if (args.items) return args.items[i];
         SegItem it;
-        const long long lo = (long long)i * args.tiles / args.nseg;
-        const long long hi = (long long)(i + 1) * args.tiles / args.nseg;
         it.set_base = 0;
-        it.a = lo * C::kT;
-        it.b = hi * C::kT < args.n ? hi * C::kT : args.n;
+        it.a = seg_a(i);
+        it.b = seg_b(i);
         it.set = 0;
         it.c = i;
         it.nseg = args.nseg;
@@ -234,6 +234,17 @@ struct Warp {
         it.slot0 = 0;
         it.pad = i;  // stage slot
         return it;
+    }
+
+    // Single set: point range [seg_a(c), seg_b(c)) of segment c.
+    __device__ long long seg_a(int c) const
+    {
+        return schedule_tile0(args.sch_n1, args.sch_l1, args.sch_n2, args.sch_l2, args.tiles, c) * C::kT;
+    }
+    __device__ long long seg_b(int c) const
+    {
+        const long long e = seg_a(c + 1);
+        return e < args.n ? e : args.n;
     }
 
     __device__ SegStore store() const
@@ -310,7 +321,40 @@ struct Warp {
         R.w = rest;
     }
 
-    // Append H[from..to) to the running hood.
+    // Corner i of the running hood.
+    __device__ __forceinline__ float2 r_pt(const RState &R, int i) const
+    {
+        return i >= R.g ? rxy()[i - R.g] : R.pts[R.gout[i]];
+    }
+
+    // Brings the last spilled corners back into the window (when pops have
+    // nearly emptied it): indices from the output array, coordinates from
+    // the input.
+    __device__ void r_refill(RState &R) const
+    {
+        const int k = min(R.g, C::kRCap / 2);
+        float2 v = make_float2(0.f, 0.f);
+        int id = 0;
+        if (lane < R.w) {
+            v = rxy()[lane];
+            id = ridx()[lane];
+        }
+        __syncwarp();
+        if (lane < R.w) {
+            rxy()[k + lane] = v;
+            ridx()[k + lane] = id;
+        }
+        for (int t = lane; t < k; t += 32) {
+            const int gi = R.gout[R.g - k + t];
+            ridx()[t] = gi;
+            rxy()[t] = R.pts[gi];
+        }
+        __syncwarp();
+        R.g -= k;
+        R.w += k;
+    }
+
+    // Append H[from..to) (coordinates and indices) to the running hood.
     __device__ void r_append(RState &R, const float2 *hxy, const int *hid, int from, int to) const
     {
         int done = from;
@@ -328,8 +372,9 @@ struct Warp {
     }
 
     // Merge hood H (h >= 1 corners, all right of the running hood) into it:
-    // bridge (p, q), then R = R[0..p] ++ H[q..h).
-    __device__ __forceinline__ void r_merge(RState &R, const float2 *hxy, const int *hid, int h)
+    // the bridge (p, q) of the two hoods (mam 1-5, probing the running
+    // hood's last corners first), then R = R[0..p] ++ H[q..h) (mam 6).
+    __device__ void r_merge(RState &R, const float2 *hxy, const int *hid, int h)
     {
         if (R.g + R.w == 0) {
             r_append(R, hxy, hid, 0, h);
@@ -347,77 +392,129 @@ struct Warp {
         r_append(R, hxy, hid, pq.y, h);
     }
 
+    // Monotone-chain pushes of the listed points (in input order) onto the
+    // running hood: before a point b is pushed, the top corner a (with o
+    // below it) is popped while orient(o, a, b) >= 0, i.e. while a is not a
+    // strict right turn. Every lane runs the same steps and stores the same
+    // values, so the window needs no synchronisation between them.
+    __device__ void r_push(RState &R, const float2 *L, const int *Lid, int m)
+    {
+        int h = R.g + R.w;
+        float2 A = make_float2(0.f, 0.f), B = A;
+        if (h >= 1) B = r_pt(R, h - 1);
+        if (h >= 2) A = r_pt(R, h - 2);
+        for (int e = 0; e < m; ++e) {
+            const float2 p = L[e];
+            while (h >= 2 && orient<MODE>(pc, A, B, p) >= 0) {
+                --h;
+                if (R.w > 0) --R.w; else --R.g;
+                B = A;
+                if (h >= 2) {
+                    if (R.w < 2 && R.g > 0) r_refill(R);
+                    A = r_pt(R, h - 2);
+                }
+            }
+            if (R.w == C::kRCap) r_flush_half(R);
+            rxy()[R.w] = p;
+            ridx()[R.w] = Lid[e];
+            ++R.w;
+            ++h;
+            A = B;
+            B = p;
+        }
+        __syncwarp();
+    }
+
     // --------------------------------------------- merge of the pending list
-    // Hoods of 32-corner chunks in registers, then the paper's stages over the
-    // chunk hoods (bridge + mam 6 compaction in place), then the result into
-    // the running hood.
+    // The pending list holds candidate points in input order, all distinct.
+    // Rounds of neighbour pruning, in parallel: a live entry p whose nearest
+    // live neighbours a (before; the running hood's last corner for the
+    // first entry) and b (after) satisfy orient(a, p, b) >= 0 lies on or
+    // below the segment between two input points a <lex p <lex b, so it is
+    // not a corner. Every deletion rests on input points, so a round's
+    // deletions may all be made at once. When a round deletes nothing, every
+    // live entry is a strict right turn between its neighbours: the live
+    // entries form a convex chain, the hood of the list (the paper's stages
+    // over these points, reached by local tests). The survivors are packed
+    // and the hood is merged into the running hood by one bridge (mam 1-5)
+    // and mam 6. If the rounds run out first, the survivors are pushed one by
+    // one by the monotone chain instead.
     __device__ __forceinline__ void flush_pending(RState &R)
     {
+        constexpr int Q = C::kPCap / 32;
         const int m = pn;
         pn = 0;
         if (m == 0) return;
         float2 *L = pxy();
         int *Lid = pidx();
-        if (m <= 2) {
-            r_merge(R, L, Lid, m);
-            __syncwarp();
-            return;
+        unsigned live[Q];
+        float2 mine[Q];
+        int mid[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const bool in = q * 32 + lane < m;
+            live[q] = __ballot_sync(kFull, in);
+            mine[q] = in ? L[q * 32 + lane] : make_float2(0.f, 0.f);
+            mid[q] = in ? Lid[q * 32 + lane] : 0;
         }
-        const int nc = (m + 31) >> 5;
-        int2 *ds = desc();
-        for (int c = 0; c < nc; ++c) {
-            const int e = c * 32 + lane;
-            const int mc = min(32, m - c * 32);
-            float2 pt = make_float2(0.f, 0.f);
-            int id = 0;
-            if (lane < mc) {
-                pt = L[e];
-                id = Lid[e];
-            }
-            const int h = mc <= 2 ? mc : warp_hood_regs<MODE>(pc, pt, id, mc);
-            __syncwarp();
-            if (lane < h) {
-                L[c * 32 + lane] = pt;
-                Lid[c * 32 + lane] = id;
-            }
-            if (lane == 0) ds[c] = make_int2(c * 32, h);
-            __syncwarp();
-        }
-        for (int st = 1; st < nc; st <<= 1) {
-            for (int a = 0; a + st < nc; a += 2 * st) {
-                const int2 P = ds[a], Q = ds[a + st];
-                __syncwarp();
-                if (Q.y == 0) continue;
-                if (P.y == 0) {
-                    if (lane == 0) ds[a] = Q;
-                    __syncwarp();
-                    continue;
-                }
-                const int2 pq = bridge_warp<MODE>(pc, PtrHood{L + P.x}, P.y, PtrHood{L + Q.x}, Q.y);
-                const int dst = P.x + pq.x + 1, src = Q.x + pq.y, cnt = Q.y - pq.y;
-                for (int b0 = 0; b0 < cnt; b0 += 32) {
-                    const int k2 = b0 + lane;
-                    float2 v = make_float2(0.f, 0.f);
-                    int id = 0;
-                    if (k2 < cnt) {
-                        v = L[src + k2];
-                        id = Lid[src + k2];
+        const int h0 = R.g + R.w;
+        const bool anchor = h0 >= 1;
+        const float2 Bv = anchor ? r_pt(R, h0 - 1) : make_float2(0.f, 0.f);
+        bool convex = false;
+        for (int round = 0; round < 4; ++round) {
+            unsigned dead[Q];
+            unsigned any = 0;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                dead[q] = 0;
+                if (live[q]) {
+                    bool d = false;
+                    if ((live[q] >> lane) & 1u) {
+                        // nearest live entries before and after entry 32 q + lane
+                        int pe = -1, ne = -1;
+                        const unsigned below = live[q] & ((1u << lane) - 1u);
+                        const unsigned above = lane < 31 ? live[q] & ~((2u << lane) - 1u) : 0u;
+                        if (below) pe = q * 32 + 31 - __clz(below);
+#pragma unroll
+                        for (int r = q - 1; r >= 0; --r)
+                            if (pe < 0 && live[r]) pe = r * 32 + 31 - __clz(live[r]);
+                        if (above) ne = q * 32 + __ffs(above) - 1;
+#pragma unroll
+                        for (int r = q + 1; r < Q; ++r)
+                            if (ne < 0 && live[r]) ne = r * 32 + __ffs(live[r]) - 1;
+                        if (ne >= 0 && (pe >= 0 || anchor)) {
+                            const float2 a = pe >= 0 ? L[pe] : Bv;
+                            d = orient<MODE>(pc, a, mine[q], L[ne]) >= 0;
+                        }
                     }
-                    __syncwarp();
-                    if (k2 < cnt) {
-                        L[dst + k2] = v;
-                        Lid[dst + k2] = id;
-                    }
-                    __syncwarp();
+                    dead[q] = __ballot_sync(kFull, d);
+                    any |= dead[q];
                 }
-                if (lane == 0) ds[a] = make_int2(P.x, pq.x + 1 + cnt);
-                __syncwarp();
             }
+            if (!any) {
+                convex = true;
+                break;
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) live[q] &= ~dead[q];
         }
-        const int2 H = ds[0];
+        // pack the live entries to the front of the list, in order
+        int base = 0;
         __syncwarp();
-        if (H.y > 0) r_merge(R, L + H.x, Lid + H.x, H.y);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if ((live[q] >> lane) & 1u) {
+                const int r = base + __popc(live[q] & ((1u << lane) - 1u));
+                L[r] = mine[q];
+                Lid[r] = mid[q];
+            }
+            base += __popc(live[q]);
+        }
         __syncwarp();
+        if (convex && base > 1)
+            r_merge(R, L, Lid, base);
+        else
+            r_push(R, L, Lid, base);
     }
 
     // Per-point elimination in one strip (not all dropped), by height: a
@@ -425,7 +522,7 @@ struct Warp {
     // after it is strictly higher. pm0 / sm0: max height before / after the
     // strip. Returns the mask of the strip's points that remain.
     __device__ __forceinline__ unsigned elim_plain(const float2 *tb, int sbase, int nvalid, float pm0,
-                                                   float sm0, float2 prev_pt, bool has_prev) const
+                                                   float sm0) const
     {
         constexpr int K = C::kK;
         float py[K];
@@ -446,47 +543,19 @@ struct Warp {
             smx = fmaxf(smx, py[j]);
         }
         surv &= nvalid >= K ? ((1u << K) - 1u) : ((1u << nvalid) - 1u);
-        if (__popc(surv) > 2) surv &= ~column_mask(tb, sbase, nvalid, prev_pt, has_prev);
         return surv;
     }
 
-    // The column rule (as in strip_corners) on a whole strip: the mask of
-    // its points that have a strictly higher point directly above them and
-    // either a point below them in their column or the set's first column to
-    // their left. Point j - 1 is tested when point j is loaded.
-    __device__ __forceinline__ unsigned column_mask(const float2 *tb, int sbase, int nvalid, float2 prev_pt,
-                                                    bool has_prev) const
+    // First occurrence and the column rule on the strip's remaining points
+    // (surv): a repeat of the previous input point goes (first occurrence
+    // wins), and so does a point with a strictly higher point directly above
+    // it when the point below it is in the same column (three collinear
+    // points) or some point lies further left (it is then strictly below the
+    // segment from the set's first point to the point above).
+    __device__ __forceinline__ unsigned point_rules(const float2 *tb, int sbase, int nvalid, unsigned surv,
+                                                    float2 prev_pt, bool has_prev) const
     {
-        constexpr int K = C::kK;
-        const float nan = __int_as_float(0x7fffffff);
-        unsigned col = 0;
-        float xb = sbase > 0 ? tb[sbase - 1].x : (has_prev ? prev_pt.x : nan);
-        float xa = nan, ya = 0.f;
-#pragma unroll 4
-        for (int j = 0; j <= K; ++j) {
-            const float2 v = j < nvalid ? tb[sbase + j] : make_float2(nan, 0.f);
-            if (j > 0) {
-                const bool up = v.x == xa && v.y > ya;
-                const bool left = xb == xa || xa > xfirst;
-                col |= (up && left ? 1u : 0u) << (j - 1);
-                xb = xa;
-            }
-            xa = v.x;
-            ya = v.y;
-        }
-        return col;
-    }
-
-    // The strip's corners among the points that remain (surv): first
-    // occurrence, the column rule, then the strip's hood by a monotone scan
-    // whose stack is a bit mask (top two corners in registers, deeper ones
-    // re-read).
-    __device__ __forceinline__ unsigned strip_corners(const float2 *tb, int sbase, int nvalid, unsigned surv,
-                                                      float2 prev_pt, bool has_prev)
-    {
-        unsigned hm = 0;
-        int hn = 0;
-        float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+        unsigned out = surv;
         while (surv) {
             const int j = __ffs(surv) - 1;
             surv &= surv - 1;
@@ -497,30 +566,14 @@ struct Warp {
                 pv = tb[sbase + j - 1];
                 hv = true;
             }
-            if (hv && same_point(pv, Pj)) continue;  // a repeat: first occurrence wins
-            // Column rule: a point with a strictly higher point directly above
-            // it is not a corner when the point below it is in the same column
-            // (three collinear points) or some point lies further left (it is
-            // then strictly below the segment from the set's first point).
-            if (j + 1 < nvalid) {
+            bool drop = hv && same_point(pv, Pj);
+            if (!drop && j + 1 < nvalid) {
                 const float2 nx = tb[sbase + j + 1];
-                if (nx.x == Pj.x && nx.y > Pj.y && ((hv && pv.x == Pj.x) || Pj.x > xfirst)) continue;
+                drop = nx.x == Pj.x && nx.y > Pj.y && ((hv && pv.x == Pj.x) || Pj.x > xfirst);
             }
-            while (hn >= 2 && orient<MODE>(pc, A, B, Pj) >= 0) {
-                hm &= ~(1u << (31 - __clz(hm)));
-                --hn;
-                B = A;
-                if (hn >= 2) {
-                    const unsigned below = hm & ~(1u << (31 - __clz(hm)));
-                    A = tb[sbase + (31 - __clz(below))];
-                }
-            }
-            if (hn >= 1) A = B;
-            B = Pj;
-            hm |= 1u << j;
-            ++hn;
+            if (drop) out &= ~(1u << j);
         }
-        return hm;
+        return out;
     }
 
     __device__ __forceinline__ void validate_strip(const float2 *tb, int sbase, int nvalid, float2 prev_pt,
@@ -600,15 +653,15 @@ struct Warp {
         }
         const bool dead = !(ymax_mine > pm0) && ymax_mine < sm0;
         const unsigned live = __ballot_sync(kFull, !dead && nvalid > 0);
-        unsigned hm = 0;
+        unsigned surv = 0;
         if (live) {
-            unsigned surv = 0;
-            bool sheared = false, done = false;
-            if (sh_skip > 0) {
+            bool sheared = false;
+            if (sh_skip > 0 && __popc(live) <= kShearBackoffLanes) {
                 --sh_skip;
             } else if (__popc(live) > kShearLanes) {
                 // Many strips survive: try the sheared frame. After a trial
-                // that does not pay, skip the next 2, 4, ... 64 tiles' trials.
+                // that does not pay, skip the next 2, 4, ... 64 tiles' trials
+                // that leave at most kShearBackoffLanes strips.
                 const unsigned long long r = sheared_tile<K>(tb, cnt, nvalid, __popc(live), prev_pt, has_prev);
                 if (r >> 32) {
                     sheared = true;
@@ -624,18 +677,11 @@ struct Warp {
                 const int L = __ffs(live) - 1;
                 const unsigned S = strip_survivors_warp(tb, cnt, L, __shfl_sync(kFull, pm0, L),
                                                         __shfl_sync(kFull, sm0, L), prev_pt, has_prev);
-                if (lane == L) {
-                    surv = S;
-                    // a hood of at most two points is the points themselves
-                    if (__popc(S) <= 2) {
-                        hm = S;
-                        done = true;
-                    }
-                }
-            } else if (!sheared && !dead && nvalid > 0) {
-                surv = elim_plain(tb, sbase, nvalid, pm0, sm0, prev_pt, has_prev);
+                if (lane == L) surv = S;
+            } else {
+                if (!sheared && !dead && nvalid > 0) surv = elim_plain(tb, sbase, nvalid, pm0, sm0);
+                if (surv) surv = point_rules(tb, sbase, nvalid, surv, prev_pt, has_prev);
             }
-            if (surv && !done) hm = strip_corners(tb, sbase, nvalid, surv, prev_pt, has_prev);
         }
         if (args.validate && nvalid > 0) validate_strip(tb, sbase, nvalid, prev_pt, has_prev);
 
@@ -643,40 +689,19 @@ struct Warp {
         prev_pt = tb[cnt - 1];
         has_prev = true;
 
-        const unsigned with = __ballot_sync(kFull, hm != 0);
+        // The remaining points go to the pending list, in input order.
+        const unsigned with = __ballot_sync(kFull, surv != 0);
         if (!with) return;
-        const int hc = __popc(hm);
-        if (__popc(with) == 1) {
-            // one lane holds all the corners: it appends them itself
-            const int L = __ffs(with) - 1;
-            const int m = __shfl_sync(kFull, hc, L);
-            if (pn + m <= C::kPCap) {
-                if (lane == L) {
-                    int r = pn;
-                    unsigned bits = hm;
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        pxy()[r] = tb[sbase + j];
-                        pidx()[r] = (int)(start + sbase + j);
-                        ++r;
-                    }
-                }
-                __syncwarp();
-                pn += m;
-                if (pn >= 32) flush_pending(R);
-                return;
-            }
-        }
+        const int hc = __popc(surv);
         const int incl = warp_incl_sum(hc);
         const int m = __shfl_sync(kFull, incl, 31);
         const int rank0 = incl - hc;
         for (int r0 = 0; r0 < m;) {
             if (pn == C::kPCap) flush_pending(R);
             const int take = min(C::kPCap - pn, m - r0);
-            if (hm) {
+            if (surv && rank0 < r0 + take && rank0 + hc > r0) {
                 int r = rank0;
-                unsigned bits = hm;
+                unsigned bits = surv;
                 while (bits) {
                     const int j = __ffs(bits) - 1;
                     bits &= bits - 1;
@@ -691,13 +716,12 @@ struct Warp {
             pn += take;
             r0 += take;
         }
-        if (pn >= 32) flush_pending(R);
     }
 
     // Survivors of strip L of a tile (the only strip not dropped whole),
     // tested by the whole warp, lane j holding the strip's point j: the
     // height rule (pm0 / sm0: max height before / after the strip), first
-    // occurrence and the column rule, as elim_plain and strip_corners apply
+    // occurrence and the column rule, as elim_plain and point_rules apply
     // them. Returns the mask of the strip's remaining points (all lanes).
     __device__ __forceinline__ unsigned strip_survivors_warp(const float2 *tb, int cnt, int L, float pm0,
                                                              float sm0, float2 prev_pt, bool has_prev) const
@@ -819,26 +843,728 @@ struct Warp {
         }
         bool last = false;
         publish(it, item_index, R, pm_carry, last);
-        if (!last && R.g == 0) {
-            if (args.items) {
-                pair_bridges(it, item_index, count);
-            } else {
-                // single set: after the CTA's warps are done, unless this
-                // CTA merges
-                pp_item = item_index;
-                pp_count = count;
-            }
-        }
-        if (last) {
-            if (args.items) {
-                // batched: the other warps are busy with other sets; merge alone
-                merge_set(it, item_index, 1, 0);
-            } else if (lane == 0) {
-                // single set: the whole CTA merges once its warps are done
-                *cta_flag() = item_index + 1;
-            }
-        }
+        // Batched: the second publisher of each neighbouring pair bridges it;
+        // the warp that completes the set merges alone (the other warps are
+        // busy with other sets).
+        if (!last && R.g == 0) pair_bridges(it, item_index, count);
+        if (last) merge_set(it, item_index, 1, 0);
         return true;
+    }
+
+    // ------------------------------------------- single set: tile stream
+    struct Stream {
+        unsigned issued;  // ring sequence number of the next tile to issue
+        int sI, kI, MI;   // segment being issued, its next tile, its tile count
+        long long aI, bI; // its point range
+        int next;         // lane 0: the next segment, claimed when this one's last tile was issued
+        bool dry;         // no segment left to claim
+    };
+
+    // Issue tiles until `limit` (exclusive ring sequence) or the input runs
+    // out, claiming segments as the previous one is fully issued. Slot
+    // metadata: tile start, point count, segment | first << 30 | last << 31.
+    __device__ void fill(Stream &st, unsigned limit, const float2 *P)
+    {
+        while (st.issued < limit) {
+            if (st.kI == st.MI) {
+                if (st.dry) break;
+                const int c = __shfl_sync(kFull, st.next, 0);
+                if (c >= args.nseg) {
+                    st.dry = true;
+                    break;
+                }
+                st.sI = c;
+                st.aI = seg_a(c);
+                st.bI = seg_b(c);
+                st.MI = (int)((st.bI - st.aI + C::kT - 1) / C::kT);
+                st.kI = 0;
+                if (st.MI == 0) {  // (segments are never empty)
+                    st.dry = true;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                const long long start = st.aI + (long long)st.kI * C::kT;
+                const int cnt = (int)(st.bI - start < C::kT ? st.bI - start : C::kT);
+                issue(P, st.aI, st.bI, st.kI, st.issued);
+                const unsigned fl = (st.kI == 0 ? 1u << 30 : 0u) | (st.kI == st.MI - 1 ? 1u << 31 : 0u);
+                meta()[st.issued % C::kS] = make_int4((int)start, cnt, (int)((unsigned)st.sI | fl), 0);
+                // the segment's last tile is issued: claim the next segment
+                // now; the atomic completes while this warp works through the
+                // tiles in its ring, and its result is read at the next fill
+                if (st.kI == st.MI - 1)
+                    st.next = min(args.nseg, (int)gridDim.x * C::kW) + (int)atomicAdd(&args.hdr->claim, 1u);
+            }
+            ++st.kI;
+            ++st.issued;
+        }
+        __syncwarp();
+    }
+
+    // Single set: the warp streams the tiles of the segments it claims, in
+    // claim order (which is input order), through its ring; the look-ahead
+    // tile may belong to the next claimed segment (its points are later input
+    // points, so they are valid witnesses for the elimination rule), and so
+    // may the running maximum of earlier points. Each segment gets its own
+    // running hood, published at its end.
+    __device__ bool run_stream(unsigned &seq)
+    {
+        const float2 *P = reinterpret_cast<const float2 *>(args.points);
+        int32_t *out = args.out_idx;
+        xfirst = P[0].x;
+        sh_skip = 0;
+        sh_fail = 0;
+        Stream st;
+        st.issued = seq;
+        st.sI = -1;
+        st.kI = 0;
+        st.MI = 0;
+        st.aI = st.bI = 0;
+        // The first segments go one per warp in warp order; the rest are
+        // claimed from the call's counter as warps become free.
+        const int nstatic = min(args.nseg, (int)gridDim.x * C::kW);
+        const int gwarp = blockIdx.x * C::kW + (threadIdx.x >> 5);
+        st.next = gwarp;
+        if (gwarp >= nstatic && lane == 0) st.next = nstatic + (int)atomicAdd(&args.hdr->claim, 1u);
+        st.dry = false;
+        const unsigned base = seq;
+        fence_proxy_async_smem();
+        __syncwarp();
+        fill(st, base + C::kS, P);
+        if (st.issued == base) {
+            warp_done();
+            return true;
+        }
+
+        RState R{0, 0, out, P};
+        float pm_carry = neg_inf(), seg_max = neg_inf();
+        float2 prev_pt = make_float2(0.f, 0.f);
+        bool has_prev = false;
+        long long last_end = -1;
+        float ymax_prev = neg_inf(), tmax_prev = neg_inf();
+        for (unsigned i = base;; ++i) {
+            const bool have = i < st.issued;
+            float ymax_cur = neg_inf(), ynext = neg_inf();
+            if (have) {
+                const int bi = i % C::kS;
+                const bool ok = mbar_wait_bounded(bars() + bi, (i / C::kS) & 1u, kWaitNs);
+                if (!__all_sync(kFull, ok)) {
+                    record_status(&args.hdr->status, kStTimeout);
+                    drain(i, st.issued);
+                    seq = st.issued;
+                    return false;
+                }
+                const int4 mt = meta()[bi];
+                ymax_cur = strip_max(buf(bi) + tile_shift(P, mt.x), mt.y);
+                ynext = warp_max(ymax_cur);
+            }
+            if (i > base) {
+                const int4 md = meta()[(i - 1) % C::kS];
+                const long long start = md.x;
+                const int cnt = md.y;
+                const unsigned fl = (unsigned)md.z;
+                if (fl & (1u << 30)) {
+                    // first tile of a segment: a new running hood
+                    R = RState{0, 0, out + start, P};
+                    pn = 0;
+                    seg_max = neg_inf();
+                    if (start != last_end) {
+                        has_prev = start > 0;
+                        prev_pt = start > 0 ? P[start - 1] : make_float2(0.f, 0.f);
+                    }
+                }
+                decide(buf((i - 1) % C::kS) + tile_shift(P, start), cnt, start, ymax_prev, tmax_prev, ynext,
+                       pm_carry, prev_pt, has_prev, R);
+                seg_max = fmaxf(seg_max, tmax_prev);
+                last_end = start + cnt;
+                __syncwarp();
+                if (fl & (1u << 31)) end_segment_single((int)(fl & 0x3fffffffu), R, seg_max);
+                fill(st, i + C::kS, P);
+            }
+            if (!have) break;
+            ymax_prev = ymax_cur;
+            tmax_prev = ynext;
+        }
+        seq = st.issued;
+        warp_done();
+        return true;
+    }
+
+    // A warp whose stream has ended (every segment it claimed is published)
+    // counts itself; the last of all the grid's warps marks its CTA as the
+    // one that leads the final merge (every segment is published by then).
+    __device__ void warp_done()
+    {
+        if (args.nseg <= 1) return;
+        __threadfence();
+        __syncwarp();
+        unsigned old = 0;
+        if (lane == 0) old = atomicAdd(args.arrivals, 1u);
+        old = __shfl_sync(kFull, old, 0);
+        if (old == gridDim.x * (unsigned)C::kW - 1u) {
+            __threadfence();
+            if (lane == 0) *cta_flag() = 1;
+        }
+    }
+
+    // End of segment c of the single set: its hood is the running hood.
+    // With one segment it is the answer; otherwise it is published (indices
+    // in the output array; coordinates and indices also staged in the
+    // workspace when it fits one window), with its count and the segment's
+    // maximum y. They become visible to the merge through warp_done's fence.
+    __device__ void end_segment_single(int c, RState &R, float seg_max)
+    {
+        flush_pending(R);
+        write_r(R);
+        const int count = R.g + R.w;
+        if (args.nseg == 1) {
+            if (lane == 0) args.out_count[0] = count;
+            return;
+        }
+        const SegStore ss = store();
+        if (R.g == 0) {
+            float2 *dst = ss.xy + (size_t)c * C::kRCap;
+            int *dsti = ss.sidx + (size_t)c * C::kRCap;
+            for (int k = lane; k < R.w; k += 32) {
+                dst[k] = rxy()[k];
+                dsti[k] = ridx()[k];
+            }
+        }
+        if (lane == 0) {
+            ss.count[c] = R.g == 0 ? count : -count - 1;  // negative: coordinates not staged
+            ss.ymax[c] = seg_max;
+        }
+        __syncwarp();
+    }
+
+    // ------------------------------------------- single set: final merge
+    // Bounded wait, by one thread of the CTA, until *word == tag; the CTA's
+    // other threads wait at the barrier. Polls back off (up to ~1 us) so that
+    // a grid of waiting CTAs does not crowd the line in L2. Returns false
+    // (in every thread) if the wait timed out or another part of the call
+    // recorded an error.
+    __device__ bool cta_wait_tag(const unsigned *word, unsigned want) const
+    {
+        __shared__ int s_ok;
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            const uint64_t t0 = global_ns();
+            unsigned nap = 32;
+            for (uint32_t it = 0;; ++it) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(word) : "memory");
+                if (v == want) break;
+                if (*reinterpret_cast<volatile int *>(&args.hdr->status) != 0 || global_ns() - t0 > kWaitNs) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(nap);
+                if (nap < 1024) nap <<= 1;
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+
+    __device__ void release_tag(unsigned *word) const
+    {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(word), "r"(tag) : "memory");
+    }
+
+    // Bridges of adjacent hoods of the list, spread over every warp of the
+    // grid: pair k is (list[k], list[k + 1]). Each warp counts its pairs
+    // once they are stored.
+    __device__ void pair_work(float2 *stg)
+    {
+        const float2 *P = reinterpret_cast<const float2 *>(args.points);
+        const SegStore ss = store();
+        WsHeader *hdr = args.hdr;
+        const int nl = (int)__ldcg(&hdr->nlist);
+        const int gwarp = blockIdx.x * C::kW + (threadIdx.x >> 5), nwarps = gridDim.x * C::kW;
+        int done = 0;
+        for (int k0 = gwarp; k0 < nl - 1; k0 += 32 * nwarps) {
+            // this warp's next 32 pairs, one per lane: their hoods and sizes
+            // in two rounds of loads
+            const int kl = k0 + lane * nwarps;
+            const bool valid = kl < nl - 1;
+            const int c = valid ? __ldcg(args.list_lid + kl) : 0, d = valid ? __ldcg(args.list_lid + kl + 1) : 0;
+            const int rc = valid ? __ldcg(ss.count + c) : 0, rd = valid ? __ldcg(ss.count + d) : 0;
+            const int m = min(32, (nl - 1 - k0 + nwarps - 1) / nwarps);
+            for (int e = 0; e < m; ++e) {
+                const int ce = __shfl_sync(kFull, c, e), de = __shfl_sync(kFull, d, e);
+                const int rce = __shfl_sync(kFull, rc, e), rde = __shfl_sync(kFull, rd, e);
+                const int2 pq = bridge_hoods(ss, P, args.out_idx, 0, ce, rce, seg_a(ce), de, rde, seg_a(de), stg);
+                if (lane == 0) {
+                    __stcg(args.list_bp + k0 + e * nwarps, pq.x);
+                    __stcg(args.list_bq + k0 + e * nwarps, pq.y);
+                }
+                ++done;
+            }
+        }
+        if (done && lane == 0) {
+            __threadfence();
+            atomicAdd(&hdr->pair_done, (unsigned)done);
+        }
+        __syncwarp();
+    }
+
+    // Copy of the kept hood ranges listed in the plan, from the staged
+    // indices to their places in the output; entries spread over all warps.
+    __device__ void copy_plan()
+    {
+        const SegStore ss = store();
+        const int np = (int)__ldcg(&args.hdr->nplan);
+        const int gwarp = blockIdx.x * C::kW + (threadIdx.x >> 5), nwarps = gridDim.x * C::kW;
+        for (int k0 = gwarp; k0 < np; k0 += 32 * nwarps) {
+            // this warp's next 32 entries, one per lane, in one round of loads
+            const int kl = k0 + lane * nwarps;
+            const int4 mine = kl < np ? __ldcg(args.plan + kl) : make_int4(0, 0, 0, 0);
+            const int m = min(32, (np - k0 + nwarps - 1) / nwarps);
+            for (int e = 0; e < m; e += 4) {
+                // four entries' loads in flight before their stores
+                int v[4][C::kRCap / 32];
+                int4 pe[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    pe[q] = make_int4(__shfl_sync(kFull, mine.x, (e + q) & 31), __shfl_sync(kFull, mine.y, (e + q) & 31),
+                                      __shfl_sync(kFull, mine.z, (e + q) & 31), __shfl_sync(kFull, mine.w, (e + q) & 31));
+                    if (e + q >= m) pe[q].z = 0;
+                    const int *src = ss.sidx + (size_t)pe[q].x * C::kRCap + pe[q].y;
+#pragma unroll
+                    for (int u = 0; u < C::kRCap / 32; ++u)
+                        if (lane + 32 * u < pe[q].z) v[q][u] = __ldcg(src + lane + 32 * u);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int u = 0; u < C::kRCap / 32; ++u)
+                        if (lane + 32 * u < pe[q].z) args.out_idx[pe[q].w + lane + 32 * u] = v[q][u];
+            }
+        }
+    }
+
+    // The warps of a CTA that does not lead the merge (every warp of it calls
+    // this): help with the pair bridges once the hood list is out, then with
+    // the copy once the plan is.
+    __device__ void merge_help()
+    {
+        if (!cta_wait_tag(&args.hdr->phase1, tag)) return;
+        pair_work(buf(0));
+        if (!cta_wait_tag(&args.hdr->phase2, tag)) return;
+        copy_plan();
+    }
+
+    // Loads n ints from global memory (L2) into shared memory, every thread
+    // keeping U loads in flight (consecutive threads, consecutive words).
+    template <int U>
+    __device__ __forceinline__ static void cta_load(int *dst, const int *src, int n, int t, int nthreads)
+    {
+        for (int b0 = 0; b0 < n; b0 += nthreads * U) {
+            int v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = b0 + u * nthreads + t;
+                if (i < n) v[u] = __ldcg(src + i);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = b0 + u * nthreads + t;
+                if (i < n) dst[i] = v[u];
+            }
+        }
+    }
+
+    // Block-wide exclusive prefix sums over entries 0..n-1 (n <=
+    // kMaxSegSingle) in order: thread t holds the contiguous entries
+    // [t M, t M + M) in registers. f(i) is entry i's value; g(i, before)
+    // receives its exclusive prefix. Returns the total. Every thread of the
+    // CTA calls it.
+    template <class F, class G>
+    __device__ int cta_scan(int n, int t, int gw, int *xsum, F f, G g) const
+    {
+        constexpr int nw = C::kW, nthreads = nw * 32;
+        constexpr int M = (kMaxSegSingle + nthreads - 1) / nthreads;
+        const int c0 = t * M;
+        int v[M];
+        int sum = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            v[j] = c0 + j < n ? f(c0 + j) : 0;
+            sum += v[j];
+        }
+        const int incl = warp_incl_sum(sum);
+        if (lane == 31) xsum[gw] = incl;
+        __syncthreads();
+        int before = incl - sum, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int x = xsum[w];
+            if (w < gw) before += x;
+            total += x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (c0 + j < n) g(c0 + j, before);
+            before += v[j];
+        }
+        return total;
+    }
+
+    // The CTA whose warp finished last leads the merge of the segment hoods
+    // (every warp of it calls this; gw = its warp index):
+    //  1. hood staircase over all segments: a segment is dropped whole when
+    //     its max y is at most the max of all earlier segments and below the
+    //     max of some later one (its points lie on or below a segment between
+    //     two input points); the others form the hood list;
+    //  2. the bridges of all adjacent hoods of the list (mam 1-5): when the
+    //     listed hoods fit in shared memory this CTA computes them there;
+    //     otherwise the list is published and every warp of the grid
+    //     bridges its share of the pairs;
+    //  3. hood i keeps its corners from the left bridge's corner s_i to the
+    //     right bridge's corner e_i; if s_i > e_i, or s_i == e_i and that
+    //     corner is not a strict right turn between the two bridges, hood i
+    //     lies on or below the segment joining its neighbours' bridge corners
+    //     and is dropped; its live neighbours become adjacent (links skip the
+    //     dropped hoods) and are bridged, and so on;
+    //  4. the kept ranges are laid out in order (mam 6): this CTA copies
+    //     them when the result is small; otherwise it publishes a plan and
+    //     every warp of the grid copies planned ranges (ranges of hoods too
+    //     large to be staged are moved within the output array first, here).
+    __device__ __noinline__ void merge_lead(int gw)
+    {
+        const float2 *P = reinterpret_cast<const float2 *>(args.points);
+        int32_t *out = args.out_idx;
+        const SegStore ss = store();
+        WsHeader *hdr = args.hdr;
+        const int nh = args.nseg;
+        constexpr int nw = C::kW;
+        constexpr int nthreads = nw * 32;
+        constexpr int M = (kMaxSegSingle + nthreads - 1) / nthreads;
+        const int t = gw * 32 + lane;
+        unsigned char *cta_base = base - C::kWarpBytes * gw;
+        constexpr size_t kStg = 2 * C::kRCap * sizeof(float2);
+        constexpr size_t kCtaBytes = C::kWarpBytes * C::kW;
+        constexpr size_t kScratch = kCtaBytes - nw * kStg;
+        float2 *stg = reinterpret_cast<float2 *>(cta_base + kCtaBytes - (size_t)(gw + 1) * kStg);
+        // control words and cross-warp slots at the start of shared memory
+        int *ctl = reinterpret_cast<int *>(cta_base);  // [0] smem hoods, [1] pairs ok
+        float *xpre = reinterpret_cast<float *>(ctl + 8);
+        float *xsuf = xpre + 32;
+        int *xsum = reinterpret_cast<int *>(xsuf + 32);
+        int *sm = xsum + 32;  // scratch ints
+        const size_t sm_ints = (kScratch - (size_t)(8 + 96) * 4) / 4;
+        static_assert((size_t)11 * kMaxSegSingle + 1 <= (kScratch - (size_t)(8 + 96) * 4) / 4,
+                      "the merge's arrays fit in shared memory");
+
+        // 1. staircase: thread t takes segments [t M, t M + M) in registers
+        int *rv = sm;  // segment counts (to the end)
+        int *lid = sm + nh;  // the hood list
+        int nl = 0;
+        {
+            const int c0 = t * M;
+            float y[M];
+            int r[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                y[j] = neg_inf();
+                r[j] = 0;
+                if (c0 + j < nh) {
+                    y[j] = __ldcg(ss.ymax + c0 + j);
+                    r[j] = __ldcg(ss.count + c0 + j);
+                }
+            }
+            float bm = neg_inf();
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                bm = fmaxf(bm, y[j]);
+                if (c0 + j < nh) rv[c0 + j] = r[j];
+            }
+            const float ip = warp_incl_prefix_max(bm), is = warp_incl_suffix_max(bm);
+            if (lane == 31) xpre[gw] = ip;
+            if (lane == 0) xsuf[gw] = is;
+            __syncthreads();
+            float before = __shfl_up_sync(kFull, ip, 1), later = __shfl_down_sync(kFull, is, 1);
+            if (lane == 0) before = neg_inf();
+            if (lane == 31) later = neg_inf();
+            for (int w = 0; w < gw; ++w) before = fmaxf(before, xpre[w]);
+            for (int w = gw + 1; w < nw; ++w) later = fmaxf(later, xsuf[w]);
+            float lat[M];
+#pragma unroll
+            for (int j = M - 1; j >= 0; --j) {
+                lat[j] = later;
+                later = fmaxf(later, y[j]);
+            }
+            unsigned keep = 0;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int cn = r[j] < 0 ? -r[j] - 1 : r[j];
+                if (cn > 0 && !(!(y[j] > before) && y[j] < lat[j])) keep |= 1u << j;
+                before = fmaxf(before, y[j]);
+            }
+            const int nk = __popc(keep);
+            const int incl = warp_incl_sum(nk);
+            if (lane == 31) xsum[gw] = incl;
+            __syncthreads();
+            int k = incl - nk;
+            for (int w = 0; w < nw; ++w) {
+                if (w < gw) k += xsum[w];
+                nl += xsum[w];
+            }
+            __syncthreads();
+            while (keep) {
+                const int j = __ffs(keep) - 1;
+                keep &= keep - 1;
+                lid[k++] = c0 + j;
+            }
+        }
+        // list arrays after the list: 9 nl + 1 ints; then the listed hoods'
+        // corners when they fit
+        int *bp = lid + nl, *bq = bp + nl, *pv = bq + nl, *dead = pv + nl, *kill = dead + nl;
+        int *nxt = kill + nl, *prv = nxt + nl, *hb = prv + nl, *pos = hb + nl;  // pos: nl + 1
+        const size_t arr_end = (size_t)nh + 10 * (size_t)nl + 1;
+        const size_t hs_off = (arr_end + 3) & ~(size_t)3;
+        float2 *hstore = reinterpret_cast<float2 *>(sm + hs_off);
+        const long long store_cap = hs_off + 4 <= sm_ints ? (long long)(sm_ints - hs_off) / 2 : 0;
+        __syncthreads();
+        {
+            int hs = 0;
+            bool unstaged = false;
+            for (int i = t; i < nl; i += nthreads) {
+                const int r = rv[lid[i]];
+                hs += r < 0 ? -r - 1 : r;
+                unstaged |= r < 0;
+                nxt[i] = i + 1 < nl ? i + 1 : -1;
+                prv[i] = i - 1;
+                dead[i] = 0;
+            }
+            const bool any_unstaged = __syncthreads_or(unstaged);
+            hs = __reduce_add_sync(kFull, (unsigned)hs);
+            if (lane == 0) xsum[gw] = hs;
+            __syncthreads();
+            if (t == 0) {
+                long long htot = 0;
+                for (int w = 0; w < nw; ++w) htot += xsum[w];
+                ctl[0] = !any_unstaged && htot <= store_cap;
+            }
+            __syncthreads();
+        }
+        const bool smem = ctl[0] != 0;
+
+        if (smem) {
+            // 2 (in this CTA). The listed hoods' corners, copied in by warps
+            // (one hood per warp at a time); the pairs are bridged below.
+            cta_scan(nl, t, gw, xsum, [&](int i) { return rv[lid[i]]; }, [&](int i, int before) { hb[i] = before; });
+            __syncthreads();
+            for (int i = gw; i < nl; i += nw) {
+                const int c = lid[i];
+                const int h = rv[c];
+                const float2 *src = ss.xy + (size_t)c * C::kRCap;
+                float2 v[C::kRCap / 32];
+#pragma unroll
+                for (int u = 0; u < C::kRCap / 32; ++u)
+                    if (lane + 32 * u < h) v[u] = __ldcg(src + lane + 32 * u);
+#pragma unroll
+                for (int u = 0; u < C::kRCap / 32; ++u)
+                    if (lane + 32 * u < h) hstore[hb[i] + lane + 32 * u] = v[u];
+            }
+            for (int i = t; i < nl; i += nthreads) pv[i] = 0;
+            if (t == 0) {
+                hdr->nlist = 0;  // nothing for the other warps to bridge
+                hdr->pair_done = 0;
+            }
+            __syncthreads();
+            if (t == 0) release_tag(&hdr->phase1);
+        } else {
+            // 2 (with the grid). Publish the list; every warp bridges its
+            // share of the pairs.
+            for (int i = t; i < nl; i += nthreads) __stcg(args.list_lid + i, lid[i]);
+            if (t == 0) {
+                hdr->nlist = (unsigned)nl;
+                hdr->pair_done = 0;
+            }
+            __syncthreads();
+            if (t == 0) release_tag(&hdr->phase1);
+            pair_work(stg);
+            if (t == 0) {
+                int ok = 1;
+                if (nl > 1) {
+                    const uint64_t t0 = global_ns();
+                    for (uint32_t it = 0;; ++it) {
+                        unsigned v;
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];"
+                                     : "=r"(v)
+                                     : "l"(&hdr->pair_done)
+                                     : "memory");
+                        if ((int)v >= nl - 1) break;
+                        if ((it & 63u) == 63u &&
+                            (*reinterpret_cast<volatile int *>(&hdr->status) != 0 || global_ns() - t0 > kWaitNs)) {
+                            record_status(&hdr->status, kStTimeout);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                ctl[1] = ok;
+            }
+            __syncthreads();
+            if (!ctl[1]) return;
+            cta_load<16>(bp, args.list_bp, nl - 1, t, nthreads);
+            cta_load<16>(bq, args.list_bq, nl - 1, t, nthreads);
+            for (int i = t; i < nl; i += nthreads) pv[i] = i + 1 < nl;
+            __syncthreads();
+        }
+
+        // 3. drop rounds over the linked list
+        auto corner = [&](int i, int j) -> float2 {
+            if (smem) return hstore[hb[i] + j];
+            const int c = lid[i];
+            return seg_hood(ss, P, out, 0, c, seg_a(c), rv[c]).pt(j);
+        };
+        for (int round = 0; round < nh + 1; ++round) {
+            // live hoods whose pair with the next live hood has no bridge:
+            // warp gw takes hoods gw + nw (32 j + l), found 32 at a time
+            for (int j0 = 0; gw + nw * j0 < nl; j0 += 32) {
+                const int i1 = gw + nw * (j0 + lane);
+                unsigned need = __ballot_sync(kFull, i1 < nl && !dead[i1] && nxt[i1] >= 0 && !pv[i1]);
+                while (need) {
+                    const int i = gw + nw * (j0 + __ffs(need) - 1);
+                    need &= need - 1;
+                    const int k = nxt[i];
+                    const int c = lid[i], d = lid[k];
+                    int2 pq;
+                    if (smem && rv[c] <= 32 && rv[d] <= 32)
+                        pq = bridge_small<MODE>(pc, FlatHood{hstore + hb[i]}, rv[c], FlatHood{hstore + hb[k]}, rv[d]);
+                    else if (smem)
+                        pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[i]}, rv[c], FlatHood{hstore + hb[k]}, rv[d]);
+                    else
+                        pq = bridge_hoods(ss, P, out, 0, c, rv[c], seg_a(c), d, rv[d], seg_a(d), stg);
+                    if (lane == 0) {
+                        bp[i] = pq.x;
+                        bq[i] = pq.y;
+                        pv[i] = 1;
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            int drop = 0;
+            for (int i = t; i < nl; i += nthreads) {
+                int dd = 0;
+                const int p = prv[i], k = nxt[i];
+                if (!dead[i] && p >= 0 && k >= 0) {
+                    const int si = bq[p], ei = bp[i];
+                    if (si > ei) {
+                        dd = 1;
+                    } else if (si == ei) {
+                        const float2 A = corner(p, bp[p]);
+                        const float2 Bc = corner(i, si);
+                        const float2 Cc = corner(k, bq[i]);
+                        dd = orient<MODE>(pc, A, Bc, Cc) >= 0;
+                    }
+                }
+                kill[i] = dd;
+                drop |= dd;
+            }
+            if (!__syncthreads_or(drop)) break;
+            for (int i = t; i < nl; i += nthreads) dead[i] |= kill[i];
+            __syncthreads();
+            // relink the live hoods past the dropped ones (the links of
+            // dropped hoods stay as they were, so the chains end at live hoods)
+            for (int i = t; i < nl; i += nthreads) {
+                if (dead[i]) continue;
+                int k = nxt[i];
+                while (k >= 0 && dead[k]) k = nxt[k];
+                int p = prv[i];
+                while (p >= 0 && dead[p]) p = prv[p];
+                kill[i] = k;  // kill[] reused: the new next
+                pos[i] = p;   // pos[] reused: the new previous
+            }
+            __syncthreads();
+            for (int i = t; i < nl; i += nthreads) {
+                if (dead[i]) continue;
+                if (kill[i] != nxt[i]) pv[i] = 0;
+                nxt[i] = kill[i];
+                prv[i] = pos[i];
+            }
+            __syncthreads();
+        }
+
+        // 4. kept range [s_i, e_i] of live hood i and its place in the output
+        bool unstaged = false;
+        for (int i = t; i < nl; i += nthreads) unstaged |= !dead[i] && rv[lid[i]] < 0;
+        const bool any_unstaged = __syncthreads_or(unstaged);
+        auto s_of = [&](int i) { return prv[i] >= 0 ? bq[prv[i]] : 0; };
+        auto range_len = [&](int i) {
+            if (dead[i]) return 0;
+            const int r = rv[lid[i]];
+            const int hi = r < 0 ? -r - 1 : r;
+            const int ei = nxt[i] >= 0 ? bp[i] : hi - 1;
+            return ei - s_of(i) + 1;
+        };
+        const int total_out = cta_scan(nl, t, gw, xsum, range_len, [&](int i, int before) { pos[i] = before; });
+        if (t == 0) pos[nl] = total_out;
+        __syncthreads();
+        const bool here = !any_unstaged && total_out <= 8 * nthreads;
+        if (here) {
+            // small result: copied by this CTA from the staged indices, a
+            // hood per warp at a time
+            for (int i = gw; i < nl; i += nw) {
+                if (dead[i]) continue;
+                const int len = pos[i + 1] - pos[i];
+                const int *src = ss.sidx + (size_t)lid[i] * C::kRCap + s_of(i);
+                for (int k = lane; k < len; k += 32) out[pos[i] + k] = __ldcg(src + k);
+            }
+        } else {
+            // plan entries (staged live hoods), copied by every warp after the release
+            for (int i = t; i < nl; i += nthreads) {
+                const int len = dead[i] || rv[lid[i]] < 0 ? 0 : pos[i + 1] - pos[i];
+                __stcg(args.plan + i, make_int4(lid[i], dead[i] ? 0 : s_of(i), len, pos[i]));
+            }
+            if (any_unstaged) {
+                // hoods whose indices are only in the output array: moved in
+                // place, in batches whose destinations all lie below every
+                // source in the batch (destinations never exceed sources)
+                int i0 = 0;
+                while (i0 < nl && dead[i0]) ++i0;
+                while (i0 < nl) {
+                    const long long a0 = seg_a(lid[i0]) + s_of(i0);
+                    int i1 = i0 + 1;
+                    while (i1 < nl && (long long)pos[i1 + 1] <= a0) ++i1;
+                    for (int i = i0 + gw; i < i1; i += nw) {
+                        if (dead[i]) continue;
+                        const int c = lid[i];
+                        if (rv[c] >= 0) continue;
+                        const long long ac = seg_a(c);
+                        const int si = s_of(i);
+                        const int len = pos[i + 1] - pos[i], dst = pos[i];
+                        if ((long long)dst == ac + si) continue;  // already in place
+                        for (int b0 = 0; b0 < len; b0 += 32) {
+                            const int k = b0 + lane;
+                            int v = 0;
+                            if (k < len) v = __ldcg(out + ac + si + k);
+                            __syncwarp();
+                            if (k < len) out[dst + k] = v;
+                            __syncwarp();
+                        }
+                    }
+                    __threadfence_block();
+                    __syncthreads();
+                    i0 = i1;
+                    while (i0 < nl && dead[i0]) ++i0;
+                }
+            }
+        }
+        if (t == 0) {
+            args.out_count[0] = total_out;
+            hdr->nplan = here ? 0u : (unsigned)nl;
+            *args.arrivals = 0;
+        }
+        __syncthreads();
+        if (t == 0) release_tag(&hdr->phase2);
+        if (!here) copy_plan();
     }
 
     // End of a segment of a multi-segment set: publish the segment hood (its
@@ -898,7 +1624,8 @@ struct Warp {
             const int ro = __ldcg(ss.count + it.slot0 + o);
             if (ro < 0) continue;  // the other hood is not staged
             const int rl = side == 0 ? ro : count, rr = side == 0 ? count : ro;
-            const int2 pq = bridge_hoods(ss, P, out, stage0, it, item_index, l, rl, l + 1, rr, buf(0));
+            const int2 pq = bridge_hoods(ss, P, out, stage0, l, rl, seg_start(it, item_index, l), l + 1, rr,
+                                         seg_start(it, item_index, l + 1), buf(0));
             if (lane == 0)
                 __stcg(ss.bridge + stage0 + l,
                        ((unsigned long long)tag << 32) | ((unsigned long long)pq.x << 16) | (unsigned)pq.y);
@@ -930,9 +1657,8 @@ struct Warp {
     // Bridge of published hoods c (left) and d (right). When both have their
     // coordinates staged, they are first copied into shared memory at stg
     // (2 RCAP corners; one round of global loads) and searched there.
-    __device__ int2 bridge_hoods(const SegStore &ss, const float2 *P, const int32_t *out, int stage0,
-                                 const SegItem &it, int item_index, int c, int rc, int d, int rd,
-                                 float2 *stg)
+    __device__ int2 bridge_hoods(const SegStore &ss, const float2 *P, const int32_t *out, int stage0, int c,
+                                 int rc, long long a_c, int d, int rd, long long a_d, float2 *stg)
     {
         const int hc = rc < 0 ? -rc - 1 : rc, hd = rd < 0 ? -rd - 1 : rd;
         if (rc >= 0 && rd >= 0 && hc <= 32 && hd <= 32)
@@ -960,8 +1686,8 @@ struct Warp {
             __syncwarp();
             return pq;
         }
-        const SegHood A = seg_hood(ss, P, out, stage0, c, seg_start(it, item_index, c), rc);
-        const SegHood B = seg_hood(ss, P, out, stage0, d, seg_start(it, item_index, d), rd);
+        const SegHood A = seg_hood(ss, P, out, stage0, c, a_c, rc);
+        const SegHood B = seg_hood(ss, P, out, stage0, d, a_d, rd);
         return bridge_warp<MODE>(pc, A, hc, B, hd);
     }
 
@@ -978,7 +1704,7 @@ struct Warp {
     __device__ long long seg_start(const SegItem &it, int item_index, int c) const
     {
         if (args.items) return args.items[item_index - it.c + c].a;
-        return ((long long)c * args.tiles / args.nseg) * C::kT;
+        return seg_a(c);
     }
 
     // Merge the published segment hoods of a set into its output, with nw
@@ -1215,7 +1941,8 @@ struct Warp {
                 else if (smem)
                     pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[c]}, rv[c], FlatHood{hstore + hb[d]}, rv[d]);
                 else
-                    pq = bridge_hoods(ss, P, out, stage0, it, item_index, c, rv[c], d, rv[d], stg);
+                    pq = bridge_hoods(ss, P, out, stage0, c, rv[c], seg_start(it, item_index, c), d, rv[d],
+                                      seg_start(it, item_index, d), stg);
                 if (lane == 0) {
                     bp[i] = pq.x;
                     bq[i] = pq.y;
@@ -1388,7 +2115,6 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
     __syncthreads();
 
     Wk.tag = (__ldcg(&args.hdr->epoch) + 1u) ^ kTagMix;
-    Wk.pp_item = -1;
 
     // Test hook: one bounded wait on a barrier that nothing completes.
     bool go = true;
@@ -1423,23 +2149,23 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
             }
         }
     } else {
-        const int nitems = args.items ? args.num_items : args.nseg;
-        const int gw = blockIdx.x * C::kW + warp, nw = gridDim.x * C::kW;
-        for (int i = gw; i < nitems; i += nw)
-            if (!Wk.run_segment(i, seq)) break;
-        // The CTA whose warp completed the set's last segment merges the
-        // segment hoods with all its warps (every other warp is done).
-        __syncthreads();
+        // Single set: warps claim segments dynamically and stream them.
+        const bool ok = __syncthreads_and(Wk.run_stream(seq));
+        // The CTA whose warp completed the last segment leads the merge of the
+        // segment hoods with all its warps; every other warp helps with the
+        // pair bridges and the final copy.
         const int flag = *Wk.cta_flag();
-        if (!flag && Wk.pp_item >= 0) Wk.pair_bridges(Wk.item(Wk.pp_item), Wk.pp_item, Wk.pp_count);
-        if (flag) {
-            // the merge reuses the CTA's shared memory, barriers included
-            if (lane == 0)
-                for (int s = 0; s <= C::kS; ++s) mbar_inval(bars + s);
-            __syncthreads();
-            __threadfence();
-            const SegItem it = Wk.item(flag - 1);
-            Wk.merge_set(it, flag - 1, C::kW, warp);
+        if (args.nseg > 1 && ok) {
+            if (flag) {
+                // the merge reuses the CTA's shared memory, barriers included
+                if (lane == 0)
+                    for (int s = 0; s <= C::kS; ++s) mbar_inval(bars + s);
+                __syncthreads();
+                __threadfence();
+                Wk.merge_lead(warp);
+            } else {
+                Wk.merge_help();
+            }
         }
     }
 
@@ -1464,6 +2190,7 @@ __global__ void __launch_bounds__(C::kNT, 1) fused_kernel(FusedArgs args)
         __threadfence();
         if (atomicAdd(&args.hdr->done_ctas, 1u) == gridDim.x - 1) {
             args.hdr->done_ctas = 0;
+            args.hdr->claim = 0;
             args.hdr->epoch = args.hdr->epoch + 1u;
         }
     }
@@ -1502,9 +2229,9 @@ static cudaError_t occupancy_cfg(int *blocks)
 
 // The tile configurations (index 1..kNumTileCfgs in the ABI): warps per CTA,
 // points per lane (odd), tile buffers per warp, running window, pending list.
-using Cfg1 = Cfg<8, 23, 4, 128, 64>;
-using Cfg2 = Cfg<12, 15, 4, 128, 64>;
-using Cfg3 = Cfg<8, 31, 3, 128, 64>;
-using Cfg4 = Cfg<6, 31, 4, 128, 64>;
+using Cfg1 = Cfg<8, 23, 4, 128, 128>;
+using Cfg2 = Cfg<12, 15, 4, 128, 128>;
+using Cfg3 = Cfg<8, 31, 3, 128, 128>;
+using Cfg4 = Cfg<6, 31, 4, 128, 128>;
 
 }  // namespace wg

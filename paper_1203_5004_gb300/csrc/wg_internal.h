@@ -13,7 +13,16 @@ struct WsHeader {
                                    // mbarrier that nothing completes, for this many ns
     unsigned long long tests;      // orientation tests (count_predicates = 1)
     unsigned long long fallbacks;  // float64 recomputations (count_predicates = 1)
-    unsigned long long pad[28];
+    unsigned long long pad[24];
+    // single-set schedule and final merge (reset within every call)
+    unsigned claim;                // segments claimed by warps (reset by the last CTA)
+    unsigned phase1;               // tag of the call whose hood list is ready
+    unsigned phase2;               // tag of the call whose output plan is ready
+    unsigned pair_work;            // pair bridges taken
+    unsigned pair_done;            // pair bridges finished
+    unsigned nlist;                // hoods left after the staircase
+    unsigned nplan;                // plan entries (kept hoods)
+    unsigned spare;
     unsigned epoch;                // calls completed on this workspace (tags of this call: epoch + 1)
     unsigned done_ctas;            // CTAs of the running call that have finished
 };
@@ -35,10 +44,17 @@ struct FusedArgs {
     const float *points;     // (x, y) pairs
     int32_t *out_idx;
     int32_t *out_count;      // per set
-    // single-set plan (items == nullptr): segments of `tiles_per_seg`-ish tiles
+    // single-set plan (items == nullptr): segments claimed dynamically by
+    // warps; segment c covers tiles [tile0(c), tile0(c + 1)) with
+    // sch_n1 segments of sch_l1 tiles, then sch_n2 of sch_l2, then single tiles
     long long n;
     int tiles;
     int nseg;
+    int sch_n1, sch_l1, sch_n2, sch_l2;
+    int *list_lid;            // single set: hoods left after the staircase (segment ids)
+    int *list_bp;             // ... bridge of the pair (i, i + 1): corner of hood i
+    int *list_bq;             // ... and of hood i + 1
+    int4 *plan;               // single set: kept hoods (stage slot, first corner, length, destination)
     // explicit items (batched), else nullptr
     const SegItem *items;
     int num_items;
@@ -62,6 +78,10 @@ struct FusedArgs {
 // (the running window of every tile configuration has this size).
 constexpr int kStageCorners = 128;
 
+// Most segments of one single-set call (the final merge keeps per-segment
+// arrays of this size in one CTA's shared memory).
+constexpr int kMaxSegSingle = 4096;
+
 // Tile configurations (warps per CTA, points per lane (odd), tile buffers
 // per warp, running window). Index 1..kNumTileCfgs as exposed in the ABI.
 struct TileCfgDesc {
@@ -74,6 +94,76 @@ constexpr TileCfgDesc kTileCfgs[kNumTileCfgs] = {
     {8, 31, 3, 128},
     {6, 31, 4, 128},
 };
+
+// Single-set schedule: the first n1 segments (one per warp) have l1 tiles,
+// the next n2 have l2 tiles, the rest one tile each, so that segments get
+// shorter towards the end of the input and the warps that claim them last
+// finish close together. At most max_seg segments.
+struct Schedule {
+    int n1, l1, n2, l2, nseg;
+};
+
+// balanced = true: one segment per warp instead, the tiles split as evenly
+// as possible (the first tiles % warps segments one tile longer).
+inline Schedule make_schedule(long long tiles, long long warps, int max_seg, bool balanced = false)
+{
+    Schedule s{0, 1, 0, 1, 0};
+    if (balanced) {
+        long long n = warps < max_seg ? warps : max_seg;
+        if (n > tiles) n = tiles;
+        if (n < 1) n = 1;
+        const long long q = tiles / n, r = tiles % n;
+        s.n1 = (int)r;
+        s.l1 = (int)(q + 1);
+        s.n2 = (int)(n - r);
+        s.l2 = (int)q;
+        s.nseg = (int)n;
+        return s;
+    }
+    if (tiles <= max_seg) {
+        s.n1 = (int)tiles;
+        s.nseg = (int)tiles;
+        return s;
+    }
+    long long n1 = warps < max_seg / 2 ? warps : max_seg / 2;
+    if (n1 < 1) n1 = 1;
+    long long l1 = (long long)(0.78 * (double)tiles / (double)n1);
+    if (l1 < 1) l1 = 1;
+    if (n1 * l1 > tiles) l1 = tiles / n1;
+    const long long rem = tiles - n1 * l1;
+    long long n3 = n1 / 4 < rem ? n1 / 4 : rem;
+    const long long r2 = rem - n3;
+    const long long room = max_seg - n1 - n3;
+    long long l2 = room > 0 ? (r2 + room - 1) / room : r2;
+    if (l2 < 1) l2 = 1;
+    // the last partial group of l2 tiles becomes single tiles: grow l2 until
+    // every segment fits
+    long long n2 = r2 / l2;
+    while (n1 + n2 + (rem - n2 * l2) > max_seg) {
+        ++l2;
+        n2 = r2 / l2;
+    }
+    n3 = rem - n2 * l2;
+    s.n1 = (int)n1;
+    s.l1 = (int)l1;
+    s.n2 = (int)n2;
+    s.l2 = (int)l2;
+    s.nseg = (int)(n1 + n2 + n3);
+    return s;
+}
+
+// First tile of segment c under a schedule (c may equal nseg: returns tiles).
+__host__ __device__ inline long long schedule_tile0(int n1, int l1, int n2, int l2, long long tiles, int c)
+{
+    long long t;
+    if (c <= n1)
+        t = (long long)c * l1;
+    else if (c <= n1 + n2)
+        t = (long long)n1 * l1 + (long long)(c - n1) * l2;
+    else
+        t = (long long)n1 * l1 + (long long)n2 * l2 + (c - n1 - n2);
+    return t < tiles ? t : tiles;
+}
 
 // Plain full-stage path.
 struct PlainArgs {

@@ -41,6 +41,7 @@ namespace {
 // spare words) | per segment: count, max y, merge scratch (16 ints), staged
 // hood coordinates and indices (kStageCorners), pair word, pair bridge.
 constexpr int kNoAllocSegments = 2048;
+static_assert(kNoAllocSegments <= kMaxSegSingle, "the final merge holds at most kMaxSegSingle segments");
 constexpr size_t kNaOffArrivals = offsetof(WsHeader, pad);
 constexpr size_t kNaOffCount = 256;
 constexpr size_t kNaOffYmax = kNaOffCount + 4 * (size_t)kNoAllocSegments;
@@ -49,7 +50,11 @@ constexpr size_t kNaOffXy = kNaOffLive + 64 * (size_t)kNoAllocSegments;
 constexpr size_t kNaOffSidx = kNaOffXy + 8 * (size_t)kStageCorners * kNoAllocSegments;
 constexpr size_t kNaOffPair = kNaOffSidx + 4 * (size_t)kStageCorners * kNoAllocSegments;
 constexpr size_t kNaOffBridge = kNaOffPair + 4 * (size_t)kNoAllocSegments;
-constexpr size_t kNaBytes = kNaOffBridge + 8 * (size_t)kNoAllocSegments;  // about 3.3 MB
+constexpr size_t kNaOffLid = kNaOffBridge + 8 * (size_t)kNoAllocSegments;
+constexpr size_t kNaOffBp = kNaOffLid + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaOffBq = kNaOffBp + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaOffPlan = kNaOffBq + 4 * (size_t)kNoAllocSegments;
+constexpr size_t kNaBytes = kNaOffPlan + 16 * (size_t)kNoAllocSegments;  // about 3.4 MB
 // Bytes that every call must see as zero: the status word, the counters and
 // the arrival count of the last-segment merge. The call counter after them
 // (and the pair words it tags) must survive from call to call.
@@ -106,9 +111,9 @@ extern "C" wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32
     const int T = fused_tile_points(kNaTileCfg);
     const int W = fused_warps(kNaTileCfg);
     const long long tiles = (n + T - 1) / T;
-    const long long warps = (long long)std::max(1, blocks) * prop.multiProcessorCount * W;
-    const long long nseg = std::min<long long>(std::min<long long>(tiles, warps), kNoAllocSegments);
-    const int grid = (int)((nseg + W - 1) / W);
+    const long long resident = (long long)std::max(1, blocks) * prop.multiProcessorCount;
+    const Schedule sch = make_schedule(tiles, resident * W, kNoAllocSegments);
+    const int grid = (int)std::min<long long>(resident, (sch.nseg + W - 1) / W);
 
     char *w = static_cast<char *>(ws);
     FusedArgs a;
@@ -118,7 +123,15 @@ extern "C" wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32
     a.out_count = out_count;
     a.n = n;
     a.tiles = (int)tiles;
-    a.nseg = (int)nseg;
+    a.nseg = sch.nseg;
+    a.sch_n1 = sch.n1;
+    a.sch_l1 = sch.l1;
+    a.sch_n2 = sch.n2;
+    a.sch_l2 = sch.l2;
+    a.list_lid = reinterpret_cast<int *>(w + kNaOffLid);
+    a.list_bp = reinterpret_cast<int *>(w + kNaOffBp);
+    a.list_bq = reinterpret_cast<int *>(w + kNaOffBq);
+    a.plan = reinterpret_cast<int4 *>(w + kNaOffPlan);
     a.hdr = reinterpret_cast<WsHeader *>(w);
     a.arrivals = reinterpret_cast<unsigned *>(w + kNaOffArrivals);
     a.seg_count = reinterpret_cast<int *>(w + kNaOffCount);

@@ -318,3 +318,34 @@ def test_batched_matches_per_set():
         a, b = offs[s], offs[s + 1]
         ref = oracle.upper_hull(ps.kx[a:b], ps.ky[a:b])
         assert out[a:a + counts[s]].tolist() == ref.tolist()
+
+
+# ---------------------------------------------------------------- strip-parallel baseline
+@pytest.mark.parametrize("kind", ["uniform", "arc", "band", "gauss_x", "gauss_disk", "columns", "duplicates"])
+def test_strips_equal_chain(kind):
+    # The strip-parallel run (the CPU baseline) must give the single scan's
+    # index list for every strip count, including strips that cut through
+    # runs of repeats and columns, and strips of one or two points.
+    for n in (0, 1, 2, 3, 4, 9, 33, 500, 4099, 70_001):
+        ps = inputs.make(kind, n, 40 + n)
+        ref = oracle.upper_hull(ps.kx, ps.ky)
+        for t in (1, 2, 3, 5, 8, 16, 64):
+            assert np.array_equal(oracle.upper_hull_strips(ps.kx, ps.ky, t), ref), (kind, n, t)
+
+
+def test_strips_cut_inside_repeat_runs():
+    # every strip boundary falls inside a long run of one repeated point, and
+    # the chain's end points are repeats too
+    kx = np.repeat(np.array([0, 5, 9, 14, 20], np.int32), 37)
+    ky = np.repeat(np.array([3, 11, 12, 8, 1], np.int32), 37)
+    ref = oracle.upper_hull_brute(kx, ky)
+    assert ref.tolist() == [0, 37, 74, 111, 148]
+    for t in range(1, 40):
+        assert oracle.upper_hull_strips(kx, ky, t).tolist() == ref.tolist(), t
+
+
+def test_strips_concave_closed_form():
+    # every point of the closed-form concave sequence is a corner, whatever the strips
+    ps = inputs.closed_form()
+    for t in (2, 7, 16, 100):
+        assert np.array_equal(oracle.upper_hull_strips(ps.kx, ps.ky, t), np.arange(4096))
