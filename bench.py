@@ -13,9 +13,13 @@ value      = points processed by all ranks / (max over ranks of the timed
              stream around K steps after W warm-up steps.
 e2e        = the same metric through wg_upper_hood_from_host: pinned host
              points copied in, corners and count copied out, every step.
-roofline   = algorithmic bytes (8n in + 4h + 4 out) per launch / average
-             launch time, against the measured HBM copy bandwidth.
-cpu_baseline = the CPU oracle (monotone chain, one core) on the same input.
+roofline   = algorithmic bytes (8n in + 4h + 4 out) per launch / median
+             launch time (>= 20 launches, CUDA events on both sides of each,
+             in a loop after the timed one), against the measured HBM copy
+             bandwidth.
+cpu_baseline = the CPU oracle's monotone chain run strip-parallel on every
+             host core, on the same input (the single-thread time is
+             reported beside it).
 
 Under torchrun (N > 1) every rank hulls its own set of the same size (weak
 scaling, no collective on the data path).
@@ -217,6 +221,23 @@ def time_oracle(ps, budget_s: float = 12.0, max_reps: int = 20):
     return len(ps) * reps / el / 1e9, reps, el
 
 
+def time_oracle_strips(ps, budget_s: float = 8.0, max_reps: int = 40):
+    """The oracle's chain run strip-parallel on every host core (one strip
+    per core, then one chain over the strip hoods), repeated on the full
+    input. Returns (Gpoints/s, reps, seconds, cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.upper_hull_strips(ps.kx[:1000], ps.ky[:1000], cores)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.upper_hull_strips(ps.kx, ps.ky, cores)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= max_reps:
+            break
+    return len(ps) * reps / el / 1e9, reps, el, cores
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle timed as the step, on this workload."""
     if rank != 0:
@@ -401,9 +422,13 @@ def run_batched(args, world, rank, local):
             pg.destroy_process_group()
         return
     import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.upper_hull_batched_threads(ps.kx, ps.ky, offs, cores)
+    cpu_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.upper_hull_batched(ps.kx, ps.ky, offs)
-    cpu_s = time.perf_counter() - t0
+    cpu1_s = time.perf_counter() - t0
     peak, peak_kind = measured_peak()
     alg = 8 * total + 4 * hsum + 8 * (S + 1) + 4 * S
     per_point = profiled_traffic_per_point("batched")
@@ -427,8 +452,11 @@ def run_batched(args, world, rank, local):
                 "counts_equal": e2e_same},
         "gpu_launches": 3 * K,
         "clocks": clocks,
-        "cpu_baseline": {"value": S / cpu_s, "unit": "sets/s", "cores": 1, "kind": "oracle",
-                         "sample": f"all {S} sets once, single-thread monotone chain, {cpu_s:.1f} s"},
+        "cpu_baseline": {"value": S / cpu_s, "unit": "sets/s", "cores": cores,
+                         "kind": "oracle, monotone chain per set, sets spread over the host cores",
+                         "sample": f"all {S} sets once on {cores} threads, {cpu_s:.2f} s",
+                         "single_thread": {"value": S / cpu1_s, "unit": "sets/s", "cores": 1,
+                                           "sample": f"all {S} sets once, {cpu1_s:.1f} s"}},
     }
     print(json.dumps(line), flush=True)
     if pg:
@@ -478,28 +506,35 @@ def run_ours(args, world, rank, local):
         if pg:
             pg.destroy_process_group()
         return
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     if pg:
         pg.barrier()
     torch.cuda.synchronize(dev)
+    # The timed region: K calls back to back, events only at its ends.
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for i in range(K):
-        starts[i].record(stream)
         wagener.upper_hood_into(pts, out, cnt, ws, opts)
-        ends[i].record(stream)
     t1.record(stream)
     torch.cuda.synchronize(dev)
     if pg:
         pg.barrier()
     clocks = sampler.stop()
     total_ms = t0.elapsed_time(t1)
-    launch_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
+    # Per-launch durations for the roofline, in a separate loop (an event
+    # on each side of every launch): the median of at least 20.
+    nl = max(20, min(K, 200))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    for i in range(nl):
+        starts[i].record(stream)
+        wagener.upper_hood_into(pts, out, cnt, ws, opts)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    launch_ms = float(np.median([s.elapsed_time(e) for s, e in zip(starts, ends)]))
     if wagener.device_status(ws) != 0:
         raise RuntimeError("device reported an error in the timed region")
     total_ms = max_over_ranks(total_ms, pg, dev)
@@ -569,7 +604,8 @@ def run_ours(args, world, rank, local):
     alg_bytes = 8 * n + 4 * h + 4
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload)
-    cpu_gpts, reps, el = time_oracle(ps)
+    cpu_gpts, reps, el, cores = time_oracle_strips(ps)
+    cpu1_gpts, reps1, el1 = time_oracle(ps, budget_s=6.0, max_reps=10)
     line = {
         "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -581,13 +617,17 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "fused_kernel", "alg_bytes_per_launch": alg_bytes},
+                     "kernel": "fused_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "launch_ms_median": launch_ms, "launches_timed": nl},
         "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 4 + 4 * hh},
         "gpu_launches": K,
         "clocks": clocks,
-        "cpu_baseline": {"value": cpu_gpts, "unit": "Gpoints/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full input, {reps} runs of the single-thread monotone chain, {el:.1f} s"},
+        "cpu_baseline": {"value": cpu_gpts, "unit": "Gpoints/s", "cores": cores,
+                         "kind": "oracle, strip-parallel monotone chain",
+                         "sample": f"full input, {reps} runs on {cores} threads, {el:.1f} s",
+                         "single_thread": {"value": cpu1_gpts, "unit": "Gpoints/s", "cores": 1,
+                                           "sample": f"full input, {reps1} runs, {el1:.1f} s"}},
     }
     if compare:
         line["compare"] = compare

@@ -53,6 +53,9 @@ def _load():
             lib.oracle_upper_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
             lib.oracle_upper_hull_strips.restype = ctypes.c_int64
             lib.oracle_upper_hull_strips.argtypes = [i32p, i32p, ctypes.c_int64, i32p, ctypes.c_int]
+            lib.oracle_upper_hull_batched_threads.restype = ctypes.c_int
+            lib.oracle_upper_hull_batched_threads.argtypes = [i32p, i32p, i64p, ctypes.c_int64, i32p, i32p,
+                                                              ctypes.c_int]
             lib.oracle_upper_hull_brute.restype = ctypes.c_int64
             lib.oracle_upper_hull_brute.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
             lib.oracle_orient_sign.restype = ctypes.c_int
@@ -136,6 +139,21 @@ def upper_hull_batched(kx, ky, offsets):
     _load().oracle_upper_hull_batched(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
                                       _p(offsets, ctypes.c_int64), num_sets,
                                       _p(out, ctypes.c_int32), _p(counts, ctypes.c_int32))
+    return out, counts[:num_sets].copy()
+
+
+def upper_hull_batched_threads(kx, ky, offsets, threads: int | None = None):
+    """The batched form with the sets spread over `threads` host threads (default: all cores)."""
+    kx, ky = _ints(kx, ky)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    num_sets = offsets.shape[0] - 1
+    t = int(threads) if threads else (os.cpu_count() or 1)
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    counts = np.empty(max(1, num_sets), dtype=np.int32)
+    if _load().oracle_upper_hull_batched_threads(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                                 _p(offsets, ctypes.c_int64), num_sets,
+                                                 _p(out, ctypes.c_int32), _p(counts, ctypes.c_int32), t) != 0:
+        raise RuntimeError("oracle_upper_hull_batched_threads: could not start threads")
     return out, counts[:num_sets].copy()
 
 

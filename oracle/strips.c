@@ -108,3 +108,66 @@ int64_t oracle_upper_hull_strips(const int32_t *kx, const int32_t *ky,
     free(cx); free(cy); free(gi); free(ci); free(scratch);
     return h;
 }
+
+void oracle_upper_hull_batched(const int32_t *kx, const int32_t *ky,
+                               const int64_t *offsets, int64_t num_sets,
+                               int32_t *out, int32_t *counts);
+
+struct batch_job {
+    const int32_t *kx, *ky;
+    const int64_t *offsets;
+    int64_t s0, s1;  /* sets [s0, s1) */
+    int32_t *out, *counts;
+};
+
+static void *batch_run(void *arg)
+{
+    struct batch_job *j = (struct batch_job *)arg;
+    oracle_upper_hull_batched(j->kx, j->ky, j->offsets + j->s0, j->s1 - j->s0,
+                              j->out, j->counts + j->s0);
+    return NULL;
+}
+
+/*
+ * The batched form on `threads` threads: each takes a contiguous range of
+ * sets (ranges of about equal point counts) and runs the single-set chain on
+ * each of its sets. Same output as oracle_upper_hull_batched. Returns 0, or
+ * -1 if a thread could not be started.
+ */
+int oracle_upper_hull_batched_threads(const int32_t *kx, const int32_t *ky,
+                                      const int64_t *offsets, int64_t num_sets,
+                                      int32_t *out, int32_t *counts, int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    if (num_sets < threads) threads = num_sets > 0 ? (int)num_sets : 1;
+    struct batch_job jobs[256];
+    pthread_t tid[256];
+    const int64_t total = num_sets > 0 ? offsets[num_sets] - offsets[0] : 0;
+    int64_t s = 0;
+    for (int t = 0; t < threads; ++t) {
+        /* sets until the point count reaches (t + 1) / threads of the total */
+        const int64_t goal = offsets[0] + total * (t + 1) / threads;
+        int64_t e = s;
+        while (e < num_sets && (t == threads - 1 || offsets[e] < goal)) ++e;
+        jobs[t].kx = kx;
+        jobs[t].ky = ky;
+        jobs[t].offsets = offsets;
+        jobs[t].s0 = s;
+        jobs[t].s1 = e;
+        jobs[t].out = out;
+        jobs[t].counts = counts;
+        s = e;
+    }
+    int started = 0, failed = 0;
+    for (int t = 1; t < threads; ++t) {
+        if (pthread_create(&tid[t], NULL, batch_run, &jobs[t]) != 0) {
+            failed = 1;
+            break;
+        }
+        ++started;
+    }
+    batch_run(&jobs[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(tid[t], NULL);
+    return failed ? -1 : 0;
+}

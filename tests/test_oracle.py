@@ -349,3 +349,15 @@ def test_strips_concave_closed_form():
     ps = inputs.closed_form()
     for t in (2, 7, 16, 100):
         assert np.array_equal(oracle.upper_hull_strips(ps.kx, ps.ky, t), np.arange(4096))
+
+
+def test_batched_threads_equal_batched():
+    # the multi-threaded batched baseline gives the single-thread batched output
+    ps, offs, _ = inputs.batched(700, seed=31, hi=3000)
+    ref_out, ref_cnt = oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    for t in (1, 2, 5, 16, 1000):
+        out, cnt = oracle.upper_hull_batched_threads(ps.kx, ps.ky, offs, t)
+        assert np.array_equal(cnt, ref_cnt), t
+        for s in range(len(cnt)):
+            a = offs[s]
+            assert np.array_equal(out[a:a + cnt[s]], ref_out[a:a + cnt[s]]), (t, s)
