@@ -331,7 +331,13 @@ def run_batched(args, world, rank, local):
     counts = torch.empty(max(S, 1), dtype=torch.int32, device=dev)
     ws = wagener.new_workspace(wagener.batched_workspace_size(offs), dev)
     stream = torch.cuda.current_stream(dev)
-    direct = lambda: wagener.upper_hood_batched_into(pts, offs_d, out, counts, ws)
+    if args.tile_config:
+        bopts = wagener.default_options(tile_config=args.tile_config)
+    elif args.no_autotune:
+        bopts = None
+    else:
+        bopts = wagener.autotune_batched(pts, offs_d, ws)
+    direct = lambda: wagener.upper_hood_batched_into(pts, offs_d, out, counts, ws, bopts)
     for _ in range(max(3, args.warmup)):
         direct()
     torch.cuda.synchronize(dev)
@@ -391,7 +397,7 @@ def run_batched(args, world, rank, local):
                 offs_b[b].copy_(offs_h, non_blocking=True)
                 copied[b].record(copy_stream)
             stream.wait_event(copied[b])
-            wagener.upper_hood_batched_into(pts_b[b], offs_b[b], out, counts_b[b], ws)
+            wagener.upper_hood_batched_into(pts_b[b], offs_b[b], out, counts_b[b], ws, bopts)
             counts_h[b].copy_(counts_b[b], non_blocking=True)
             done[b].record(stream)
     e2e_run(2)
@@ -439,6 +445,8 @@ def run_batched(args, world, rank, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched {S} sets, sizes log-uniform in [3, 65536], mixed kinds",
                    "sets": S, "points": total, "corners": hsum, "seed": 5,
+                   "tile_config": int(bopts.tile_config) if bopts else 0,
+                   "batch_seg_tiles": int(bopts.batch_seg_tiles) if bopts else 0,
                    "gpoints_per_s": total / (ms * 1e-3) / 1e9, "cuda_graph": True,
                    "l2": "input > 129 MB L2 (no flush)", "parallelism": f"replicas x{world}"},
         "compare": {"plain_per_set_ms_per_step": plain_ms, "plain_per_set_sets_per_s": S / (plain_ms * 1e-3),

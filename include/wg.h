@@ -84,13 +84,18 @@ typedef struct wg_options {
                                 for this many times the resident warps (1..8) */
     int32_t schedule;        /* single set: 0 = library choice; 1 = balanced (one segment per warp,
                                 equal shares); 2 = guided (long segments first, then shorter ones
-                                claimed by warps as they become free) */
-    int32_t reserved[2];
+                                claimed by warps as they become free); 3 = one CTA (balanced over
+                                the warps of a single CTA: for small inputs) */
+    int32_t batch_seg_tiles; /* batched: 0 = library choice (autotuned if wg_autotune_batched ran,
+                                else 128); else 8..4096 tiles per segment of a large set (larger
+                                sets are split over several warps) */
+    int32_t reserved[1];
 } wg_options;
 
 #define WG_NUM_TILE_CONFIGS 4
 #define WG_SCHEDULE_BALANCED 1
 #define WG_SCHEDULE_GUIDED 2
+#define WG_SCHEDULE_ONE_CTA 3
 
 /* Fills *opts with the defaults (filtered predicate, no counters, no
  * validation, library-chosen tiling). */
@@ -138,8 +143,10 @@ wg_status wg_upper_hood_plain(const float *points, int64_t n, int32_t *out_idx,
  * Many independent sets in one persistent launch. Set s is
  * points[offsets[s] .. offsets[s+1]) (each set sorted on its own); its
  * corners, as indices local to the set, go to out_idx[offsets[s] ...] and
- * their count to out_counts[s]. Sets are binned by size on the device: a warp,
- * a CTA or several CTAs per set.
+ * their count to out_counts[s]. Sets are binned by size on the device and
+ * taken from a queue by warps, largest first: a set of up to batch_seg_tiles
+ * tiles is one warp's item; a larger set is split into segments taken by
+ * several warps, and the warp that completes it merges their hoods.
  * offsets   device int64[num_sets + 1], non-decreasing, offsets[0] >= 0
  * h_offsets host copy of the same offsets (only read by the size query)
  * out_idx   device int32[max(offsets[num_sets], 1)], CSR-aligned with points
@@ -159,6 +166,9 @@ wg_status wg_upper_hood_batched(const float *points, const int64_t *offsets,
  * caller's device buffer d_points, runs wg_upper_hood_ex, and copies the count
  * and the corners back to h_out_idx / h_out_count. Synchronises `stream`.
  * d_out_idx: device int32[max(n,1)]; d_out_count: device int32[1].
+ * If the device recorded an error in the workspace (see wg_get_device_status)
+ * that status is returned (and left in the workspace) instead of WG_OK, and
+ * the host outputs are not valid.
  * ---------------------------------------------------------------------- */
 wg_status wg_upper_hood_from_host(const float *h_points, int64_t n,
                                   int32_t *h_out_idx, int32_t *h_out_count,
@@ -191,6 +201,18 @@ const char *wg_status_string(wg_status status);
 wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx,
                       int32_t *out_count, void *workspace, size_t ws_bytes,
                       wg_options *best, wg_stream_t stream);
+
+/* Autotuner of the batched form: times every tile configuration and the
+ * segment caps 16, 32 and 128 tiles on the caller's sets (a valid input for
+ * wg_upper_hood_batched, with its workspace), keeps the fastest for this
+ * device and writes it to *best. Later batched calls with tile_config = 0
+ * and batch_seg_tiles = 0 use the kept choice. Synchronises `stream`. The
+ * paper has no counterpart (tuning). */
+wg_status wg_autotune_batched(const float *points, const int64_t *offsets,
+                              int32_t num_sets, int32_t *out_idx,
+                              int32_t *out_counts, void *workspace,
+                              size_t ws_bytes, wg_options *best,
+                              wg_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Unit entry points for tests (small sizes; one warp or one CTA).
@@ -242,16 +264,18 @@ wg_status wg_debug_set_stall(void *workspace, int32_t stall_ns, wg_stream_t stre
  *
  * - The first call on a device looks up the array's device address (with
  *   that device current) and keeps it; make that first call before any
- *   stream capture.
+ *   stream capture. The kept address belongs to the device's context: do
+ *   not use this entry point after cudaDeviceReset on that device.
  * - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
  *   routine. Each call clears the part of the array that must start at zero
  *   with a cudaMemsetAsync on `stream`, then launches the fused kernel.
  * - All calls in the process share the array. Calls whose GPU work overlaps
  *   (on different streams, or from different threads) race on it and give
  *   wrong results; serialise them.
- * - Only argument and launch errors are reported. Errors found on the device
- *   (a bounded wait that timed out) are not visible here; use
- *   wg_upper_hood_ex with a workspace to read them.
+ * - Only argument and launch errors are returned. The count is set to -1
+ *   before the launch, so a call whose device work gave up (a bounded wait
+ *   that timed out) leaves a negative count; wg_upper_hood_ex with a
+ *   workspace reports such errors by name.
  * ---------------------------------------------------------------------- */
 wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32_t *out_idx,
                                 int32_t *out_count, wg_stream_t stream);

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
         ("tile_config", _i32),
         ("segments_per_cta", _i32),
         ("schedule", _i32),
-        ("reserved", _i32 * 2),
+        ("batch_seg_tiles", _i32),
+        ("reserved", _i32 * 1),
     ]
 
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "wg_read_counters": (_i32, [_vp, _vp, _vp, _vp]),
     "wg_status_string": (ctypes.c_char_p, [_i32]),
     "wg_autotune": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
+    "wg_autotune_batched": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
     "wg_debug_orient": (_i32, [_vp, _i64, _vp, _vp, _i32, _vp]),
     "wg_debug_bridge": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "wg_debug_warp_hood": (_i32, [_vp, _i32, _vp, _vp, _i32, _vp]),

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -22,7 +23,7 @@ cudaError_t plain_stage_launch(const PlainArgs &a, bool first, int mode, cudaStr
 long long plain_blocks(long long hoods);
 cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_sets,
                            int32_t *out_idx, int32_t *out_counts, void *ws, size_t ws_bytes,
-                           int cfg, int mode, int validate, cudaStream_t st);
+                           int cfg, int cap, int mode, int validate, cudaStream_t st);
 size_t batched_workspace_bytes(const int64_t *h_offsets, int num_sets);
 cudaError_t debug_orient(const float *p, long long ntri, int8_t *signs, unsigned long long *fb,
                          int fp64, cudaStream_t st);
@@ -54,9 +55,12 @@ constexpr size_t kOffListBq = kOffListBp + 4 * (size_t)kMaxSeg;
 constexpr size_t kOffPlan = kOffListBq + 4 * (size_t)kMaxSeg;
 constexpr size_t kSingleWsBytes = kOffPlan + 16 * (size_t)kMaxSeg;
 constexpr int kDefaultCfg = 1;         // single set, before any autotuning (best for small n)
-constexpr int kBatchedDefaultCfg = 3;  // batched form (measured best on the mixed 100k-set workload)
+constexpr int64_t kOneCtaMaxN = 1 << 15;  // untuned: one CTA up to this many points
+constexpr int kBatchedDefaultCfg = 3;  // batched form, before any autotuning
+constexpr int kBatchedDefaultSegTiles = 128;  // batched: tiles per segment of a large set, untuned
 
 struct DevInfo {
+    std::atomic<bool> ready{false};  // set (release) once the fields below are filled
     bool init = false;
     bool ok = false;
     int sms = 0;
@@ -67,21 +71,28 @@ std::mutex g_mu;
 DevInfo g_dev[64];
 
 // Autotuned choice per device and size bucket floor(log2 n).
-struct Tuned {
-    int cfg = 0;
-    int spc = 0;
-    int sched = 0;
-};
-Tuned g_tuned[64][33];
+// Autotuned choice per device and size bucket, packed in one word so that
+// calls read it without a lock: cfg | spc << 8 | sched << 16 (0: not tuned).
+std::atomic<int> g_tuned[64][33];
+// Batched form, per device: cfg | segment cap << 8 (0: not tuned).
+std::atomic<int> g_tuned_batched[64];
 
 inline cudaStream_t S(wg_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
-wg_status dev_info(DevInfo **out)
+// Device facts, looked up once per device (the first call takes the lock;
+// later calls read them without it). *dev_out receives the device number.
+wg_status dev_info(DevInfo **out, int *dev_out = nullptr)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WG_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev_out) *dev_out = dev;
     DevInfo &d = g_dev[dev];
+    if (d.ready.load(std::memory_order_acquire)) {
+        if (!d.ok) return WG_ERR_UNSUPPORTED;
+        *out = &d;
+        return WG_OK;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
     if (!d.init) {
         d.init = true;
         cudaDeviceProp prop;
@@ -96,6 +107,7 @@ wg_status dev_info(DevInfo **out)
             }
             d.occ[c] = b;
         }
+        d.ready.store(true, std::memory_order_release);
     }
     if (!d.ok) return WG_ERR_UNSUPPORTED;
     *out = &d;
@@ -135,7 +147,8 @@ wg_status check_opts(const wg_options &o)
     if (o.pred_mode != WG_PRED_FILTERED && o.pred_mode != WG_PRED_FP64) return WG_ERR_INVALID_VALUE;
     if (o.tile_config < 0 || o.tile_config > kNumTileCfgs) return WG_ERR_INVALID_VALUE;
     if (o.segments_per_cta < 0 || o.segments_per_cta > 8) return WG_ERR_INVALID_VALUE;
-    if (o.schedule < 0 || o.schedule > WG_SCHEDULE_GUIDED) return WG_ERR_INVALID_VALUE;
+    if (o.schedule < 0 || o.schedule > WG_SCHEDULE_ONE_CTA) return WG_ERR_INVALID_VALUE;
+    if (o.batch_seg_tiles != 0 && (o.batch_seg_tiles < 8 || o.batch_seg_tiles > 4096)) return WG_ERR_INVALID_VALUE;
     return WG_OK;
 }
 
@@ -184,19 +197,18 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     st = check_common(points, n, out_idx, out_count, workspace, ws_bytes, wg_upper_hood_workspace_size(n));
     if (st != WG_OK) return st;
     DevInfo *d = nullptr;
-    st = dev_info(&d);
+    int dev = 0;
+    st = dev_info(&d, &dev);
     if (st != WG_OK) return st;
     if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), S(stream)) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 
-    int dev = 0;
-    cudaGetDevice(&dev);
     int cfg = o.tile_config, spc = o.segments_per_cta, sched = o.schedule;
     {
-        std::lock_guard<std::mutex> lk(g_mu);
-        const Tuned &t = g_tuned[dev][bucket(n)];
-        if (cfg == 0) cfg = t.cfg ? t.cfg : kDefaultCfg;
-        if (spc == 0) spc = t.spc ? t.spc : 1;
-        if (sched == 0) sched = t.sched ? t.sched : WG_SCHEDULE_GUIDED;
+        const int t = g_tuned[dev][bucket(n)].load(std::memory_order_relaxed);
+        if (cfg == 0) cfg = (t & 0xff) ? (t & 0xff) : kDefaultCfg;
+        if (spc == 0) spc = ((t >> 8) & 0xff) ? ((t >> 8) & 0xff) : 1;
+        if (sched == 0) sched = ((t >> 16) & 0xff) ? ((t >> 16) & 0xff)
+                                                    : (n <= kOneCtaMaxN ? WG_SCHEDULE_ONE_CTA : WG_SCHEDULE_BALANCED);
     }
     // Segments are claimed dynamically by the warps of one resident wave of
     // CTAs; segments_per_cta scales the number of warps the schedule plans
@@ -204,8 +216,9 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     const int T = fused_tile_points(cfg);
     const int W = fused_warps(cfg);
     const long long tiles = (n + T - 1) / T;
-    const int resident = std::max(1, d->occ[cfg]) * d->sms;
-    const Schedule sch = make_schedule(tiles, (long long)resident * W * spc, kMaxSeg, sched == WG_SCHEDULE_BALANCED);
+    const int resident = sched == WG_SCHEDULE_ONE_CTA ? 1 : std::max(1, d->occ[cfg]) * d->sms;
+    const Schedule sch =
+        make_schedule(tiles, (long long)resident * W * spc, kMaxSeg, sched != WG_SCHEDULE_GUIDED);
     const int grid = (int)std::min<long long>(resident, (sch.nseg + W - 1) / W);
 
     FusedArgs a;
@@ -363,9 +376,13 @@ wg_status wg_upper_hood_batched(const float *points, const int64_t *offsets, int
     st = dev_info(&d);
     if (st != WG_OK) return st;
     if (num_sets == 0) return WG_OK;
-    const int cfg = o.tile_config ? o.tile_config : kBatchedDefaultCfg;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int tuned = dev >= 0 && dev < 64 ? g_tuned_batched[dev].load(std::memory_order_relaxed) : 0;
+    const int cfg = o.tile_config ? o.tile_config : ((tuned & 0xff) ? (tuned & 0xff) : kBatchedDefaultCfg);
+    const int cap = o.batch_seg_tiles ? o.batch_seg_tiles : ((tuned >> 8) ? (tuned >> 8) : kBatchedDefaultSegTiles);
     const cudaError_t e = batched_launch(points, offsets, num_sets, out_idx, out_counts, workspace,
-                                         ws_bytes, cfg, pred_mode_bits(o), o.validate, S(stream));
+                                         ws_bytes, cfg, cap, pred_mode_bits(o), o.validate, S(stream));
     if (e == cudaErrorInvalidValue) return WG_ERR_WORKSPACE;
     return e == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 }
@@ -386,6 +403,14 @@ wg_status wg_upper_hood_from_host(const float *h_points, int64_t n, int32_t *h_o
     if (cudaMemcpyAsync(h_out_count, d_out_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return WG_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return WG_ERR_CUDA;
+    // an error recorded on the device (a bounded wait that timed out) means
+    // the count and corners are not valid: report it instead
+    {
+        int dst = 0;
+        const WsHeader *hh = reinterpret_cast<const WsHeader *>(workspace);
+        if (cudaMemcpy(&dst, &hh->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return WG_ERR_CUDA;
+        if (dst != 0) return static_cast<wg_status>(dst);
+    }
     const int32_t h = *h_out_count;
     if (h < 0 || h > std::max<int64_t>(n, 1)) return WG_ERR_CUDA;
     if (h > 0 && cudaMemcpyAsync(h_out_idx, d_out_idx, (size_t)h * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -448,9 +473,11 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WG_ERR_CUDA;
     float best_ms = 1e30f;
     int best_cfg = kDefaultCfg, best_spc = 1, best_sched = WG_SCHEDULE_GUIDED;
-    const int variants[][2] = {{WG_SCHEDULE_BALANCED, 1}, {WG_SCHEDULE_GUIDED, 1}, {WG_SCHEDULE_GUIDED, 2}};
+    const int variants[][2] = {{WG_SCHEDULE_BALANCED, 1}, {WG_SCHEDULE_BALANCED, 2}, {WG_SCHEDULE_GUIDED, 1},
+                               {WG_SCHEDULE_ONE_CTA, 1}};
     for (int cfg = 1; cfg <= kNumTileCfgs; ++cfg) {
         for (const auto &var : variants) {
+            if (var[0] == WG_SCHEDULE_ONE_CTA && n > (int64_t(1) << 21)) continue;
             const int spc = var[1];
             o.tile_config = cfg;
             o.segments_per_cta = spc;
@@ -481,14 +508,64 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != WG_OK) return st;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        g_tuned[dev][bucket(n)] = Tuned{best_cfg, best_spc, best_sched};
-    }
+    g_tuned[dev][bucket(n)].store(best_cfg | best_spc << 8 | best_sched << 16, std::memory_order_relaxed);
     wg_options_default(best);
     best->tile_config = best_cfg;
     best->segments_per_cta = best_spc;
     best->schedule = best_sched;
+    return WG_OK;
+}
+
+wg_status wg_autotune_batched(const float *points, const int64_t *offsets, int32_t num_sets, int32_t *out_idx,
+                              int32_t *out_counts, void *workspace, size_t ws_bytes, wg_options *best,
+                              wg_stream_t stream)
+{
+    if (!best) return WG_ERR_INVALID_VALUE;
+    DevInfo *d = nullptr;
+    int dev = 0;
+    wg_status st = dev_info(&d, &dev);
+    if (st != WG_OK) return st;
+    cudaStream_t s = S(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return WG_ERR_CUDA;
+    wg_options o;
+    wg_options_default(&o);
+    float best_ms = 1e30f;
+    int best_cfg = kBatchedDefaultCfg, best_cap = kBatchedDefaultSegTiles;
+    const int caps[] = {16, 32, 128};
+    for (int cfg = 1; cfg <= kNumTileCfgs && st == WG_OK; ++cfg) {
+        for (int cap : caps) {
+            o.tile_config = cfg;
+            o.batch_seg_tiles = cap;
+            if ((st = wg_upper_hood_batched(points, offsets, num_sets, out_idx, out_counts, workspace, ws_bytes, &o,
+                                            stream)) != WG_OK)
+                break;
+            const int reps = 2;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps; ++r)
+                wg_upper_hood_batched(points, offsets, num_sets, out_idx, out_counts, workspace, ws_bytes, &o, stream);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = WG_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_cfg = cfg;
+                best_cap = cap;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WG_OK) return st;
+    g_tuned_batched[dev].store(best_cfg | best_cap << 8, std::memory_order_relaxed);
+    wg_options_default(best);
+    best->tile_config = best_cfg;
+    best->batch_seg_tiles = best_cap;
     return WG_OK;
 }
 

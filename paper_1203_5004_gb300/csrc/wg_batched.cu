@@ -1,11 +1,12 @@
 // wg_batched.cu -- many independent sets in one persistent launch.
 //
-// A planning kernel reads the CSR offsets on the device and turns every
+// Two planning passes read the CSR offsets on the device and turn every
 // non-empty set into work items for the fused kernel: one item (a whole set on
-// one CTA) for sets of up to kMaxTilesPerSeg tiles, several segments for
-// larger sets, whose segment hoods the last-arriving CTA merges. Items are
-// binned by size (large sets first) so the dynamic queue of the persistent
-// kernel finishes with the short items.
+// one warp) for sets of up to `cap` tiles, several segments for larger sets
+// (claimed by different warps; the warp that completes the set merges the
+// segment hoods). Items are binned by size (large sets first) so that the
+// dynamic queue of the persistent kernel finishes with the short items. The
+// segment cap is a launch parameter (the batched autotuner chooses it).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,8 +21,9 @@ cudaError_t fused_launch(int cfg, const FusedArgs &args, int grid, int mode, cud
 cudaError_t fused_occupancy(int cfg, int *blocks);
 int fused_tile_points(int cfg);
 
-constexpr int kMaxTilesPerSeg = 128;
-constexpr int kMaxSegPerSet = 2048;  // the final merge keeps 2 ints per segment in one tile buffer
+constexpr int kDefaultSegTiles = 128;  // tiles per segment of a large set (default cap)
+constexpr int kMinSegTiles = 8;        // the smallest cap a call may use (sizes the workspace)
+constexpr int kMaxSegPerSet = 2048;
 constexpr int kPlanThreads = 1024;
 constexpr int kBins = 3;
 
@@ -80,7 +82,7 @@ size_t batched_workspace_bytes(const int64_t *h_offsets, int num_sets)
         const long long n = h_offsets[s + 1] - h_offsets[s];
         if (n <= 0) continue;
         const long long tiles = (n + T - 1) / T;
-        const long long ns = std::min<long long>((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, kMaxSegPerSet);
+        const long long ns = std::min<long long>((tiles + kMinSegTiles - 1) / kMinSegTiles, kMaxSegPerSet);
         items += ns;
     }
     return batch_layout(num_sets, items, items).total;
@@ -88,13 +90,13 @@ size_t batched_workspace_bytes(const int64_t *h_offsets, int num_sets)
 
 __device__ __forceinline__ int bin_of(long long tiles) { return tiles >= 8 ? 0 : (tiles >= 2 ? 1 : 2); }
 
-// Segments of a set of n points: one per kMaxTilesPerSeg tiles (at most
+// Segments of a set of n points: one per `cap` tiles (at most
 // kMaxSegPerSet), and its size bin.
-__device__ __forceinline__ int set_segments(long long n, int T, int &bin)
+__device__ __forceinline__ int set_segments(long long n, int T, int cap, int &bin)
 {
     const long long tiles = (n + T - 1) / T;
     bin = bin_of(tiles);
-    return (int)min((tiles + kMaxTilesPerSeg - 1) / kMaxTilesPerSeg, (long long)kMaxSegPerSet);
+    return (int)min((tiles + cap - 1) / cap, (long long)kMaxSegPerSet);
 }
 
 // Planning, in two grid-wide passes. ctl: [0] items, [1] queue, [2] done,
@@ -102,7 +104,7 @@ __device__ __forceinline__ int set_segments(long long n, int T, int &bin)
 // cleared before the first pass).
 // Pass 1: items per size bin (one global add per bin and block).
 __global__ void __launch_bounds__(kPlanThreads)
-    batch_count_kernel(const int64_t *off, int num_sets, int T, int *ctl, int32_t *out_counts)
+    batch_count_kernel(const int64_t *off, int num_sets, int T, int cap, int *ctl, int32_t *out_counts)
 {
     __shared__ int s_bin[kBins];
     const int tid = threadIdx.x;
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kPlanThreads)
             continue;
         }
         int bin;
-        const int nseg = set_segments(n, T, bin);
+        const int nseg = set_segments(n, T, cap, bin);
         atomicAdd(&s_bin[bin], nseg);
     }
     __syncthreads();
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kPlanThreads)
 // first), with stage slots for sets of several segments. A block reserves
 // its ranges with one global add per bin, then places its own sets.
 __global__ void __launch_bounds__(kPlanThreads)
-    batch_assign_kernel(const int64_t *off, int num_sets, int T, SegItem *items, long long max_items,
+    batch_assign_kernel(const int64_t *off, int num_sets, int T, int cap, SegItem *items, long long max_items,
                         long long max_stage, int *ctl, int *status)
 {
     __shared__ int s_bin[kBins];
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kPlanThreads)
         const long long n = off[s + 1] - off[s];
         if (n <= 0) continue;
         int bin;
-        const int nseg = set_segments(n, T, bin);
+        const int nseg = set_segments(n, T, cap, bin);
         atomicAdd(&s_bin[bin], nseg);
         if (nseg > 1) atomicAdd(&s_stage, nseg);
     }
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kPlanThreads)
         const long long a0 = off[s], n = off[s + 1] - a0;
         if (n <= 0) continue;
         int bin;
-        const int nseg = set_segments(n, T, bin);
+        const int nseg = set_segments(n, T, cap, bin);
         const long long tiles = (n + T - 1) / T;
         const int slot0 = atomicAdd(&s_cur[bin], nseg);
         int stage = 0;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(kPlanThreads)
 }
 
 cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_sets, int32_t *out_idx,
-                           int32_t *out_counts, void *ws, size_t ws_bytes, int cfg, int mode, int validate,
+                           int32_t *out_counts, void *ws, size_t ws_bytes, int cfg, int cap, int mode, int validate,
                            cudaStream_t st)
 {
     // The item bound of the workspace, recovered from its size (every item
@@ -221,8 +223,9 @@ cudaError_t batched_launch(const float *points, const int64_t *offsets, int num_
         (int)std::max(1LL, std::min<long long>((num_sets + kPlanThreads - 1) / kPlanThreads, 4LL * std::max(1, sms)));
     cudaError_t e = cudaMemsetAsync(ctl + 3, 0, 7 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    batch_count_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, ctl, out_counts);
-    batch_assign_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, items, L.max_items,
+    if (cap < kMinSegTiles) cap = kDefaultSegTiles;
+    batch_count_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, cap, ctl, out_counts);
+    batch_assign_kernel<<<plan_blocks, kPlanThreads, 0, st>>>(offsets, num_sets, T, cap, items, L.max_items,
                                                               L.max_stage, ctl, &hdr->status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

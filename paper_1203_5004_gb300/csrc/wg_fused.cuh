@@ -41,6 +41,8 @@
 //    kept ranges are copied to the output.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 #include "wg_device.cuh"
@@ -1346,7 +1348,8 @@ struct Warp {
             if (t == 0) {
                 long long htot = 0;
                 for (int w = 0; w < nw; ++w) htot += xsum[w];
-                ctl[0] = !any_unstaged && htot <= store_cap;
+                ctl[0] = htot <= store_cap;
+                (void)any_unstaged;
             }
             __syncthreads();
         }
@@ -1355,19 +1358,39 @@ struct Warp {
         if (smem) {
             // 2 (in this CTA). The listed hoods' corners, copied in by warps
             // (one hood per warp at a time); the pairs are bridged below.
-            cta_scan(nl, t, gw, xsum, [&](int i) { return rv[lid[i]]; }, [&](int i, int before) { hb[i] = before; });
+            auto hsize = [&](int i) {
+                const int r = rv[lid[i]];
+                return r < 0 ? -r - 1 : r;
+            };
+            cta_scan(nl, t, gw, xsum, hsize, [&](int i, int before) { hb[i] = before; });
             __syncthreads();
             for (int i = gw; i < nl; i += nw) {
                 const int c = lid[i];
-                const int h = rv[c];
-                const float2 *src = ss.xy + (size_t)c * C::kRCap;
-                float2 v[C::kRCap / 32];
+                const int r = rv[c];
+                if (r >= 0) {
+                    // staged: the coordinates themselves
+                    const float2 *src = ss.xy + (size_t)c * C::kRCap;
+                    float2 v[C::kRCap / 32];
 #pragma unroll
-                for (int u = 0; u < C::kRCap / 32; ++u)
-                    if (lane + 32 * u < h) v[u] = __ldcg(src + lane + 32 * u);
+                    for (int u = 0; u < C::kRCap / 32; ++u)
+                        if (lane + 32 * u < r) v[u] = __ldcg(src + lane + 32 * u);
 #pragma unroll
-                for (int u = 0; u < C::kRCap / 32; ++u)
-                    if (lane + 32 * u < h) hstore[hb[i] + lane + 32 * u] = v[u];
+                    for (int u = 0; u < C::kRCap / 32; ++u)
+                        if (lane + 32 * u < r) hstore[hb[i] + lane + 32 * u] = v[u];
+                } else {
+                    // not staged: gathered through the indices in the output array
+                    const int h = -r - 1;
+                    const int32_t *idx = out + seg_a(c);
+                    for (int k0 = 0; k0 < h; k0 += 128) {
+                        int id[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (k0 + lane + 32 * u < h) id[u] = __ldcg(idx + k0 + lane + 32 * u);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (k0 + lane + 32 * u < h) hstore[hb[i] + k0 + lane + 32 * u] = P[id[u]];
+                    }
+                }
             }
             for (int i = t; i < nl; i += nthreads) pv[i] = 0;
             if (t == 0) {
@@ -1435,10 +1458,11 @@ struct Warp {
                     const int k = nxt[i];
                     const int c = lid[i], d = lid[k];
                     int2 pq;
-                    if (smem && rv[c] <= 32 && rv[d] <= 32)
-                        pq = bridge_small<MODE>(pc, FlatHood{hstore + hb[i]}, rv[c], FlatHood{hstore + hb[k]}, rv[d]);
+                    const int hc = rv[c] < 0 ? -rv[c] - 1 : rv[c], hd = rv[d] < 0 ? -rv[d] - 1 : rv[d];
+                    if (smem && hc <= 32 && hd <= 32)
+                        pq = bridge_small<MODE>(pc, FlatHood{hstore + hb[i]}, hc, FlatHood{hstore + hb[k]}, hd);
                     else if (smem)
-                        pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[i]}, rv[c], FlatHood{hstore + hb[k]}, rv[d]);
+                        pq = bridge_warp<MODE>(pc, FlatHood{hstore + hb[i]}, hc, FlatHood{hstore + hb[k]}, hd);
                     else
                         pq = bridge_hoods(ss, P, out, 0, c, rv[c], seg_a(c), d, rv[d], seg_a(d), stg);
                     if (lane == 0) {
@@ -2201,8 +2225,18 @@ template <class C, int MODE>
 static cudaError_t launch_cfg(const FusedArgs &args, int grid, cudaStream_t stream)
 {
     auto kern = fused_kernel<C, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kBytes);
+    // The shared-memory attribute is set once per device (it stays with the
+    // function in that device's context), not on every launch.
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kBytes);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
     kern<<<grid, C::kNT, C::kBytes, stream>>>(args);
     return cudaGetLastError();
 }

@@ -64,8 +64,20 @@ constexpr int kNaTileCfg = 3;
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNaBytes];
 
+static_assert(kNaBytes == kNaOffPlan + 16 * (size_t)kNoAllocSegments, "the fixed layout ends at kNaBytes");
+static_assert(16 * kNoAllocSegments >= 13 * kNoAllocSegments + 106,
+              "the merge scratch holds the batched merge's arrays for every segment");
+
+// Per device, filled once with that device current: the array's device
+// address, the SM count and the resident CTAs per SM.
+struct NaDevice {
+    void *ws = nullptr;
+    int sms = 0;
+    int blocks = 0;
+    bool ok = false;
+};
 std::mutex g_na_mu;
-void *g_na_ptr[64] = {nullptr};
+NaDevice g_na_dev[64];
 
 inline cudaStream_t S(wg_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -83,36 +95,47 @@ extern "C" wg_status wg_upper_hood_noalloc(const float *points, int64_t n, int32
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WG_ERR_CUDA;
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return WG_ERR_CUDA;
-    if (!(prop.major == 10 && prop.minor == 3)) return WG_ERR_UNSUPPORTED;
 
-    // Set-up, once per device, with that device current.
-    void *ws = nullptr;
+    // Set-up, once per device, with that device current: the device address
+    // of the fixed array (in host code its name is only a stand-in for the
+    // symbol), the device's SM count and the kernel's occupancy.
+    NaDevice nd;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
+        NaDevice &d = g_na_dev[dev];
+        if (!d.ws) {
+            int major = 0, minor = 0, sms = 0, blocks = 0;
+            if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return WG_ERR_CUDA;
+            if (!(major == 10 && minor == 3)) return WG_ERR_UNSUPPORTED;
+            if (fused_occupancy(kNaTileCfg, &blocks) != cudaSuccess) return WG_ERR_CUDA;
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || !p) return WG_ERR_CUDA;
-            g_na_ptr[dev] = p;
+            d.sms = sms;
+            d.blocks = std::max(1, blocks);
+            d.ok = true;
+            d.ws = p;
         }
-        ws = g_na_ptr[dev];
+        nd = d;
     }
+    void *ws = nd.ws;
 
     cudaStream_t s = S(stream);
     if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 
     // The array keeps the previous call's contents: clear the part that must
-    // start at zero.
+    // start at zero. The count starts at -1, so that a call whose device work
+    // gave up (a bounded wait that timed out) leaves a negative count.
     if (cudaMemsetAsync(ws, 0, kNaZeroBytes, s) != cudaSuccess) return WG_ERR_CUDA;
+    if (cudaMemsetAsync(out_count, 0xff, sizeof(int32_t), s) != cudaSuccess) return WG_ERR_CUDA;
 
-    int blocks = 0;
-    if (fused_occupancy(kNaTileCfg, &blocks) != cudaSuccess) return WG_ERR_CUDA;
     const int T = fused_tile_points(kNaTileCfg);
     const int W = fused_warps(kNaTileCfg);
     const long long tiles = (n + T - 1) / T;
-    const long long resident = (long long)std::max(1, blocks) * prop.multiProcessorCount;
-    const Schedule sch = make_schedule(tiles, resident * W, kNoAllocSegments);
+    const long long resident = (long long)nd.blocks * nd.sms;
+    const Schedule sch = make_schedule(tiles, resident * W, kNoAllocSegments, true);
     const int grid = (int)std::min<long long>(resident, (sch.nseg + W - 1) / W);
 
     char *w = static_cast<char *>(ws);

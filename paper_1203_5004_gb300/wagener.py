@@ -151,6 +151,20 @@ def autotune(points: torch.Tensor, workspace: torch.Tensor | None = None, stream
     return best
 
 
+def autotune_batched(points: torch.Tensor, offsets: torch.Tensor, workspace: torch.Tensor, stream=None) -> Options:
+    """wg_autotune_batched on the caller's sets (offsets: device int64 CSR)."""
+    points = _as_points(points)
+    num_sets = offsets.shape[0] - 1
+    total = points.shape[0]
+    out = torch.empty(max(total, 1), dtype=torch.int32, device=points.device)
+    counts = torch.empty(max(num_sets, 1), dtype=torch.int32, device=points.device)
+    best = Options()
+    check(load().wg_autotune_batched(_ptr(points), _ptr(offsets), num_sets, _ptr(out), _ptr(counts),
+                                     _ptr(workspace), workspace.numel(), ctypes.byref(best), _stream(stream)),
+          "wg_autotune_batched")
+    return best
+
+
 def debug_orient(triples: torch.Tensor, pred_mode: int = _lib.WG_PRED_FILTERED, stream=None):
     """Signs of orient for consecutive point triples; returns (signs int8, fallbacks)."""
     triples = _as_points(triples)

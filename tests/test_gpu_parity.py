@@ -420,6 +420,46 @@ def test_batched_full_100k(wg):
     assert np.array_equal(out[:n][valid], ref_out[:n][valid])
 
 
+@pytest.mark.slow
+def test_batched_full_100k_autotuned(wg):
+    # the batched workload at its full size through the autotuned launch the
+    # bench times (tile configuration and segment cap chosen on these sets),
+    # every set checked against the oracle
+    ps, offs, _ = inputs.batched(100_000, seed=5)
+    ref_out, ref_cnt = oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    pts = gpu_points(ps)
+    offs_d = torch.from_numpy(offs).to(DEV)
+    ws = wg.new_workspace(wg.batched_workspace_size(offs))
+    best = wg.autotune_batched(pts, offs_d, ws)
+    assert 1 <= best.tile_config <= 4 and best.batch_seg_tiles in (16, 32, 128)
+    n = int(offs[-1])
+    out = torch.empty(n, dtype=torch.int32, device=DEV)
+    cnt = torch.empty(len(offs) - 1, dtype=torch.int32, device=DEV)
+    for _ in range(2):
+        wg.upper_hood_batched_into(pts, offs_d, out, cnt, ws, best)
+    out, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+    assert_same(cnt, ref_cnt, "batched counts, autotuned")
+    valid = np.zeros(n, dtype=bool)
+    for s in np.nonzero(ref_cnt)[0]:
+        valid[offs[s]:offs[s] + ref_cnt[s]] = True
+    assert np.array_equal(out[valid], ref_out[:n][valid])
+    assert wg.device_status(ws) == 0
+
+
+@pytest.mark.parametrize("cap", [8, 16, 32])
+def test_batched_split_sets(wg, cap):
+    # small segment caps split the larger sets over several warps
+    ps, offs, _ = inputs.batched(2000, seed=41, hi=65536)
+    ref_out, ref_cnt = oracle.upper_hull_batched(ps.kx, ps.ky, offs)
+    for cfg in (2, 3):
+        out, cnt = wg.upper_hood_batched(gpu_points(ps), offs, wg.default_options(tile_config=cfg, batch_seg_tiles=cap))
+        out, cnt = out.cpu().numpy(), cnt.cpu().numpy()
+        assert_same(cnt, ref_cnt, f"batched counts cap {cap} cfg {cfg}")
+        for s in range(len(cnt)):
+            a = offs[s]
+            assert_same(out[a:a + cnt[s]], ref_out[a:a + ref_cnt[s]], f"set {s} cap {cap} cfg {cfg}")
+
+
 def test_batched_with_empty_and_large_sets(wg):
     sizes = [0, 1, 2, 0, 5, 300_000, 0, 7, 1_000_000, 3]
     sets = [inputs.make(k, n, i) for i, (k, n) in enumerate(zip(
