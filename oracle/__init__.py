@@ -5,8 +5,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its
 product path never does: the CUDA library fails loudly instead of falling back
 here.
 
-``oracle.c`` holds the arithmetic (Andrew's monotone chain and an O(n^3) brute
-force, both with exact int64 orientation). ``strips.c`` runs the same chain on
+``oracle.c`` holds the arithmetic (Andrew's monotone chain for the upper and
+lower hoods, their O(n^3) brute forces, and the convex hull stitched from the
+two chains, all with exact int64 orientation). ``strips.c`` runs the same chain on
 contiguous strips in parallel threads and once more over the strip hoods (the
 CPU baseline of the measurements). This module only compiles them with gcc,
 loads them with ctypes and marshals numpy arrays.
@@ -51,6 +52,12 @@ def _load():
             i8p = ctypes.POINTER(ctypes.c_int8)
             lib.oracle_upper_hull.restype = ctypes.c_int64
             lib.oracle_upper_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_lower_hull.restype = ctypes.c_int64
+            lib.oracle_lower_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_lower_hull_brute.restype = ctypes.c_int64
+            lib.oracle_lower_hull_brute.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            lib.oracle_convex_hull.restype = ctypes.c_int64
+            lib.oracle_convex_hull.argtypes = [i32p, i32p, ctypes.c_int64, i32p, i32p]
             lib.oracle_upper_hull_strips.restype = ctypes.c_int64
             lib.oracle_upper_hull_strips.argtypes = [i32p, i32p, ctypes.c_int64, i32p, ctypes.c_int]
             lib.oracle_upper_hull_batched_threads.restype = ctypes.c_int
@@ -86,6 +93,38 @@ def upper_hull(kx, ky) -> np.ndarray:
     out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
     h = _load().oracle_upper_hull(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
                                   kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def lower_hull(kx, ky) -> np.ndarray:
+    """Indices of the strict lower-hood corners, left to right (monotone chain)."""
+    kx, ky = _ints(kx, ky)
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    h = _load().oracle_lower_hull(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                  kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def lower_hull_brute(kx, ky) -> np.ndarray:
+    """Same set by the O(n^3) witness-pair definition (small n only)."""
+    kx, ky = _ints(kx, ky)
+    if kx.shape[0] > 2048:
+        raise ValueError("brute force is O(n^3); keep n small")
+    out = np.empty(max(1, kx.shape[0]), dtype=np.int32)
+    h = _load().oracle_lower_hull_brute(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32),
+                                        kx.shape[0], _p(out, ctypes.c_int32))
+    return out[:h].copy()
+
+
+def convex_hull(kx, ky) -> np.ndarray:
+    """Convex-hull corners clockwise from the first point: upper hood, then the
+    lower hood back without its ends."""
+    kx, ky = _ints(kx, ky)
+    n = kx.shape[0]
+    out = np.empty(max(1, n), dtype=np.int32)
+    scratch = np.empty(max(1, n), dtype=np.int32)
+    h = _load().oracle_convex_hull(_p(kx, ctypes.c_int32), _p(ky, ctypes.c_int32), n,
+                                   _p(out, ctypes.c_int32), _p(scratch, ctypes.c_int32))
     return out[:h].copy()
 
 

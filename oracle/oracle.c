@@ -8,7 +8,9 @@
  *
  * Problem (paper Section 2, "Wagener's algorithm, CUDA version"): given n
  * points presented left to right, return the corners of their upper hood
- * (upper convex hull), left to right. The paper assumes n = 2^s, no three
+ * (upper convex hull), left to right. The lower hood and the convex hull (the
+ * paper's title problem, of which Section 2 computes the upper half) follow
+ * the same rules below. The paper assumes n = 2^s, no three
  * points collinear, x in [0,1] and no rounding error; this oracle drops those
  * assumptions and fixes the readings below instead.
  *
@@ -136,4 +138,83 @@ void oracle_upper_hull_batched(const int32_t *kx, const int32_t *ky,
         int64_t a = offsets[s], n = offsets[s + 1] - a;
         counts[s] = (int32_t)oracle_upper_hull(kx + a, ky + a, n, out + a);
     }
+}
+
+/*
+ * Lower hood by the same monotone chain (the lower half of Andrew's method):
+ * scan left to right; skip a repeat of the stack top; before pushing b, pop
+ * the top a (with o below it) while orient(o, a, b) <= 0, i.e. while a is
+ * not a strict left turn. The chain runs from the first point to the
+ * first occurrence of the last point; a last column of several points gives
+ * a vertical last edge. Writes the corner indices to out[0..h), returns h.
+ */
+int64_t oracle_lower_hull(const int32_t *kx, const int32_t *ky, int64_t n,
+                          int32_t *out)
+{
+    int64_t h = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (h > 0 && kx[out[h - 1]] == kx[i] && ky[out[h - 1]] == ky[i])
+            continue;
+        while (h >= 2) {
+            int32_t o = out[h - 2], a = out[h - 1];
+            if (orient_i64(kx[o], ky[o], kx[a], ky[a], kx[i], ky[i]) <= 0)
+                --h;
+            else
+                break;
+        }
+        out[h++] = (int32_t)i;
+    }
+    return h;
+}
+
+/*
+ * Brute force of the lower hood, O(n^3): point i is a corner iff it is the
+ * first occurrence of its coordinates and there is no pair a, b with
+ * p_a <lex p_i <lex p_b and orient(p_a, p_b, p_i) >= 0 (p_i on or above the
+ * segment p_a p_b).
+ */
+int64_t oracle_lower_hull_brute(const int32_t *kx, const int32_t *ky,
+                                int64_t n, int32_t *out)
+{
+    int64_t h = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int corner = 1;
+        for (int64_t j = 0; j < i && corner; ++j)
+            if (kx[j] == kx[i] && ky[j] == ky[i])
+                corner = 0;
+        for (int64_t a = 0; a < n && corner; ++a) {
+            if (!lex_less(kx, ky, a, i))
+                continue;
+            for (int64_t b = 0; b < n; ++b) {
+                if (!lex_less(kx, ky, i, b))
+                    continue;
+                if (orient_i64(kx[a], ky[a], kx[b], ky[b], kx[i], ky[i]) >= 0) {
+                    corner = 0;
+                    break;
+                }
+            }
+        }
+        if (corner)
+            out[h++] = (int32_t)i;
+    }
+    return h;
+}
+
+/*
+ * Convex hull (the paper's title problem, Section 2 computes its upper
+ * half): the corners clockwise from the first point, i.e. the upper hood
+ * from the first point to the last, then the lower hood from the last point
+ * back to the first, without its two ends (they are the upper hood's ends).
+ * Corners are strict: collinear points are not corners; repeats count once
+ * (first occurrence). `scratch` holds n ints. Returns the corner count.
+ */
+int64_t oracle_convex_hull(const int32_t *kx, const int32_t *ky, int64_t n,
+                           int32_t *out, int32_t *scratch)
+{
+    int64_t hu = oracle_upper_hull(kx, ky, n, out);
+    int64_t hl = oracle_lower_hull(kx, ky, n, scratch);
+    int64_t h = hu;
+    for (int64_t j = hl - 2; j >= 1; --j)
+        out[h++] = scratch[j];
+    return h;
 }

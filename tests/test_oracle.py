@@ -361,3 +361,87 @@ def test_batched_threads_equal_batched():
         for s in range(len(cnt)):
             a = offs[s]
             assert np.array_equal(out[a:a + cnt[s]], ref_out[a:a + cnt[s]]), (t, s)
+
+
+# ---------------------------------------------------------------- lower hood and convex hull
+@pytest.mark.parametrize("kind", ["uniform", "arc", "band", "gauss_x", "gauss_disk", "columns", "duplicates"])
+def test_lower_chain_equals_brute_force(kind):
+    for n in (0, 1, 2, 3, 4, 7, 16, 31, 100, 200):
+        for seed in range(3):
+            ps = inputs.make(kind, n, 300 + 7 * n + seed)
+            assert np.array_equal(oracle.lower_hull(ps.kx, ps.ky), oracle.lower_hull_brute(ps.kx, ps.ky)), (kind, n)
+
+
+def test_lower_chain_lattice_exhaustive():
+    # every set of up to 5 distinct points on a 3 x 3 lattice, sorted
+    import itertools
+    pts = [(x, y) for x in range(3) for y in range(3)]
+    for k in range(1, 6):
+        for combo in itertools.combinations(pts, k):
+            kx = np.array([p[0] for p in combo], np.int32)
+            ky = np.array([p[1] for p in combo], np.int32)
+            assert np.array_equal(oracle.lower_hull(kx, ky), oracle.lower_hull_brute(kx, ky)), combo
+
+
+def test_lower_chain_is_mirrored_upper_chain_distinct_x():
+    # with distinct x values, mirroring y (ky -> G - 1 - ky) keeps the order,
+    # and the lower hood is the mirror image of the upper hood
+    r = np.random.default_rng(5)
+    for n in (3, 10, 100, 5000):
+        kx = np.sort(r.choice(inputs.G, size=n, replace=False)).astype(np.int32)
+        ky = r.integers(0, inputs.G, size=n).astype(np.int32)
+        assert np.array_equal(oracle.lower_hull(kx, ky), oracle.upper_hull(kx, inputs.G - 1 - ky))
+
+
+def test_lower_chain_closed_forms():
+    # an upward-convex parabola: every point is a lower corner, and the upper
+    # hood has only the ends
+    i = np.arange(2000, dtype=np.int64)
+    kx = i * 4000
+    ky = (i - 1000) ** 2 * 8
+    assert np.array_equal(oracle.lower_hull(kx, ky), np.arange(2000))
+    assert oracle.upper_hull(kx, ky).tolist() == [0, 1999]
+    # a last column of several points: the lower hood ends with its vertical edge
+    assert oracle.lower_hull([0, 5, 5, 5], [0, 1, 4, 9]).tolist() == [0, 1, 3]
+    # repeats count once (first occurrence)
+    assert oracle.lower_hull([0, 0, 3, 3, 6], [2, 2, 0, 0, 2]).tolist() == [0, 2, 4]
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (10, 2), (100, 3), (1000, 4), (20000, 5)])
+def test_convex_hull_matches_qhull_general_position(n, seed):
+    spatial = pytest.importorskip("scipy.spatial")
+    r = np.random.default_rng(seed)
+    kx = r.choice(inputs.G, size=n, replace=False)
+    ky = r.choice(inputs.G, size=n, replace=False)
+    kx, ky = inputs.sort_lex(kx, ky)
+    got = oracle.convex_hull(kx, ky)
+    ref = spatial.ConvexHull(np.stack([kx, ky], 1).astype(np.float64)).vertices
+    assert sorted(got.tolist()) == sorted(ref.tolist())
+    assert got[0] == 0 and len(set(got.tolist())) == len(got)
+    # clockwise: negative signed area
+    x = kx[got].astype(np.float64)
+    y = ky[got].astype(np.float64)
+    assert np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) < 0
+
+
+@pytest.mark.parametrize("kind", ["uniform", "arc", "band", "gauss_x", "columns", "duplicates"])
+def test_convex_hull_is_upper_then_lower_brute(kind):
+    # the stitched hull equals the brute-force upper corners followed by the
+    # brute-force lower corners, reversed, without the shared ends
+    for n in (1, 2, 3, 5, 40, 150):
+        ps = inputs.make(kind, n, 900 + n)
+        up = oracle.upper_hull_brute(ps.kx, ps.ky).tolist()
+        lo = oracle.lower_hull_brute(ps.kx, ps.ky).tolist()
+        assert oracle.convex_hull(ps.kx, ps.ky).tolist() == up + lo[::-1][1:-1], (kind, n)
+
+
+def test_convex_hull_degenerate():
+    assert oracle.convex_hull([], []).tolist() == []
+    assert oracle.convex_hull([7], [7]).tolist() == [0]
+    assert oracle.convex_hull([7, 7, 7], [7, 7, 7]).tolist() == [0]
+    assert oracle.convex_hull([0, 1, 2, 3], [0, 1, 2, 3]).tolist() == [0, 3]  # collinear
+    assert oracle.convex_hull([0, 0, 0], [0, 1, 2]).tolist() == [0, 2]  # one column
+    # a square with its centre and a point on an edge
+    kx = [0, 0, 1, 2, 2, 2]
+    ky = [0, 2, 1, 0, 1, 2]
+    assert oracle.convex_hull(kx, ky).tolist() == [0, 1, 5, 3]
