@@ -140,6 +140,24 @@ wg_status wg_upper_hood_plain(const float *points, int64_t n, int32_t *out_idx,
                               wg_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Convex hull: the paper's title problem, of which Section 2 computes the
+ * upper half. The corners clockwise from the first point: the upper hood
+ * from the first point to the last, then the lower hood back to the first,
+ * without its two ends. The lower hood is the upper hood of the points turned
+ * by 180 degrees ((x, y) -> (1 - 2^-24 - x, 1 - 2^-24 - y), still grid points,
+ * in reverse order, still sorted), so the call runs the fused upper-hood
+ * kernel twice with a turning pass between and a stitch after. Same input
+ * contract and readings (strict corners; a repeated point counts once, by its
+ * first occurrence).
+ * out_idx   device int32[max(n, 1)]: corners at out_idx[0..count)
+ * workspace >= wg_convex_hull_workspace_size(n) bytes, zero-filled once
+ * ---------------------------------------------------------------------- */
+size_t wg_convex_hull_workspace_size(int64_t n);
+wg_status wg_convex_hull(const float *points, int64_t n, int32_t *out_idx,
+                         int32_t *out_count, void *workspace, size_t ws_bytes,
+                         const wg_options *opts, wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Many independent sets in one persistent launch. Set s is
  * points[offsets[s] .. offsets[s+1]) (each set sorted on its own); its
  * corners, as indices local to the set, go to out_idx[offsets[s] ...] and

@@ -30,6 +30,9 @@ cudaError_t debug_orient(const float *p, long long ntri, int8_t *signs, unsigned
 cudaError_t debug_bridge(const float *P, int hp, const float *Q, int hq, int *out, int fp64,
                          cudaStream_t st);
 cudaError_t debug_warp_hood(const float *pts, int m, int *out, int *count, int fp64, cudaStream_t st);
+cudaError_t hull_turn(const float *points, float *rot, long long n, int sms, cudaStream_t st);
+cudaError_t hull_stitch(const float *points, long long n, const int32_t *lidx, const int32_t *lcount, int32_t *out,
+                        int32_t *count, int sms, cudaStream_t st);
 }  // namespace wg
 
 using namespace wg;
@@ -256,6 +259,56 @@ wg_status wg_upper_hood(const float *points, int64_t n, int32_t *out_idx, int32_
                         void *workspace, size_t ws_bytes, wg_stream_t stream)
 {
     return wg_upper_hood_ex(points, n, out_idx, out_count, workspace, ws_bytes, nullptr, stream);
+}
+
+// ------------------------------------------------------------------ convex hull
+// Workspace: the single-set workspace | turned points (8n) | lower corners
+// (4n) | lower count.
+static void hull_layout(int64_t n, size_t *off_rot, size_t *off_lidx, size_t *off_lcnt, size_t *total)
+{
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    size_t o = align_up(kSingleWsBytes, 256);
+    *off_rot = o;
+    o = align_up(o + nn * 8, 256);
+    *off_lidx = o;
+    o = align_up(o + nn * 4, 256);
+    *off_lcnt = o;
+    o = align_up(o + 4, 256);
+    *total = o;
+}
+
+size_t wg_convex_hull_workspace_size(int64_t n)
+{
+    if (n < 0) return 0;
+    size_t a, b, c, t;
+    hull_layout(n, &a, &b, &c, &t);
+    return t;
+}
+
+wg_status wg_convex_hull(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count, void *workspace,
+                         size_t ws_bytes, const wg_options *opts, wg_stream_t stream)
+{
+    if (n < 0) return WG_ERR_INVALID_VALUE;
+    wg_status st = check_common(points, n, out_idx, out_count, workspace, ws_bytes, wg_convex_hull_workspace_size(n));
+    if (st != WG_OK) return st;
+    DevInfo *d = nullptr;
+    st = dev_info(&d);
+    if (st != WG_OK) return st;
+    cudaStream_t s = S(stream);
+    if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+    size_t orot, olidx, olcnt, total;
+    hull_layout(n, &orot, &olidx, &olcnt, &total);
+    char *w = static_cast<char *>(workspace);
+    float *rot = reinterpret_cast<float *>(w + orot);
+    int32_t *lidx = reinterpret_cast<int32_t *>(w + olidx);
+    int32_t *lcnt = reinterpret_cast<int32_t *>(w + olcnt);
+    // upper hood into the caller's output, then the lower hood of the turned
+    // points into the workspace (both calls share the single-set workspace)
+    if ((st = wg_upper_hood_ex(points, n, out_idx, out_count, workspace, kSingleWsBytes, opts, stream)) != WG_OK)
+        return st;
+    if (hull_turn(points, rot, n, d->sms, s) != cudaSuccess) return WG_ERR_CUDA;
+    if ((st = wg_upper_hood_ex(rot, n, lidx, lcnt, workspace, kSingleWsBytes, opts, stream)) != WG_OK) return st;
+    return hull_stitch(points, n, lidx, lcnt, out_idx, out_count, d->sms, s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 }
 
 // ------------------------------------------------------------------ plain path

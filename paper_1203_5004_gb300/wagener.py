@@ -73,6 +73,33 @@ def upper_hood(points: torch.Tensor, opts: Options | None = None, workspace: tor
     return out[: int(cnt.item())]
 
 
+def convex_hull_workspace_size(n: int) -> int:
+    return int(load().wg_convex_hull_workspace_size(int(n)))
+
+
+def convex_hull_into(points: torch.Tensor, out_idx: torch.Tensor, out_count: torch.Tensor,
+                     workspace: torch.Tensor, opts: Options | None = None, stream=None) -> None:
+    """wg_convex_hull on caller-owned buffers (no allocation, no sync)."""
+    points = _as_points(points)
+    n = points.shape[0]
+    code = load().wg_convex_hull(_ptr(points), n, _ptr(out_idx), _ptr(out_count), _ptr(workspace),
+                                 workspace.numel(), ctypes.byref(opts) if opts else None, _stream(stream))
+    check(code, "wg_convex_hull")
+
+
+def convex_hull(points: torch.Tensor, opts: Options | None = None, workspace: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """Indices (int32, on the device) of the convex-hull corners, clockwise from the first point."""
+    points = _as_points(points)
+    n = points.shape[0]
+    dev = points.device
+    ws = workspace if workspace is not None else new_workspace(convex_hull_workspace_size(n), dev)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    convex_hull_into(points, out, cnt, ws, opts, stream)
+    return out[: int(cnt.item())]
+
+
 def upper_hood_plain(points: torch.Tensor, opts: Options | None = None, workspace: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:
     """Same result by the unfused schedule (one launch per stage)."""

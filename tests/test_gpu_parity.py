@@ -536,3 +536,28 @@ def test_autotune_keeps_results(wg):
     assert 1 <= best.tile_config <= 4
     got = wg.upper_hood(pts).cpu().numpy()
     assert_same(got, oracle.upper_hull(ps.kx, ps.ky), "after autotune")
+
+
+# ---------------------------------------------------------------- convex hull
+@pytest.mark.parametrize("kind", KINDS)
+def test_convex_hull_small_and_tile_edges(wg, kind):
+    ws = wg.new_workspace(wg.convex_hull_workspace_size(1 << 20))
+    sizes = list(range(0, 120)) + [479, 480, 481, 991, 992, 993, 5000, 100_003, 1 << 20]
+    for n in sizes:
+        ps = inputs.make(kind, n, 500 + n)
+        pts = gpu_points(ps) if n else torch.empty((0, 2), dtype=torch.float32, device=DEV)
+        got = wg.convex_hull(pts, workspace=ws).cpu().numpy()
+        assert_same(got, oracle.convex_hull(ps.kx, ps.ky), f"hull {kind} n={n}")
+    assert wg.device_status(ws) == 0
+
+
+@pytest.mark.parametrize("name,make", [
+    ("2^24 uniform", lambda: inputs.uniform(1 << 24, 2)),
+    ("2^24 arc", lambda: inputs.arc(1 << 24, 3)),
+    ("closed form", lambda: inputs.closed_form()),
+    ("2^26 band", lambda: inputs.band(1 << 26, 4)),
+])
+def test_convex_hull_configs(wg, name, make):
+    ps = make()
+    got = wg.convex_hull(gpu_points(ps)).cpu().numpy()
+    assert_same(got, oracle.convex_hull(ps.kx, ps.ky), f"hull {name}")
