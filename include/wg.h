@@ -254,6 +254,14 @@ wg_status wg_debug_orient(const float *points, int64_t ntri, int8_t *signs,
 wg_status wg_debug_bridge(const float *P, int32_t hp, const float *Q,
                           int32_t hq, int32_t *d_pq, int32_t pred_mode,
                           wg_stream_t stream);
+/* wg_debug_bridge_cta: the same bridge by one CTA of 256 threads with the
+ *   multi-level bracketing search (the paper's closing section: samples of P
+ *   at decreasing intervals, here one corner per warp per round, each with a
+ *   32-way search of its tangent corner on Q), for hoods of many thousands of
+ *   corners. d_pq[0] = p, d_pq[1] = q. */
+wg_status wg_debug_bridge_cta(const float *P, int32_t hp, const float *Q,
+                              int32_t hq, int32_t *d_pq, int32_t pred_mode,
+                              wg_stream_t stream);
 wg_status wg_debug_warp_hood(const float *points, int32_t m, int32_t *d_out,
                              int32_t *d_out_count, int32_t pred_mode,
                              wg_stream_t stream);

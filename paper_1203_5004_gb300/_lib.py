@@ -63,6 +63,7 @@ SIGNATURES = {
     "wg_debug_orient": (_i32, [_vp, _i64, _vp, _vp, _i32, _vp]),
     "wg_debug_bridge": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "wg_debug_warp_hood": (_i32, [_vp, _i32, _vp, _vp, _i32, _vp]),
+    "wg_debug_bridge_cta": (_i32, [_vp, _i32, _vp, _i32, _vp, _i32, _vp]),
     "wg_debug_set_stall": (_i32, [_vp, _i32, _vp]),
     "wg_upper_hood_noalloc": (_i32, [_vp, _i64, _vp, _vp, _vp]),
     "wg_version": (ctypes.c_char_p, []),

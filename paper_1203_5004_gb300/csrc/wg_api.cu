@@ -30,6 +30,7 @@ cudaError_t debug_orient(const float *p, long long ntri, int8_t *signs, unsigned
 cudaError_t debug_bridge(const float *P, int hp, const float *Q, int hq, int *out, int fp64,
                          cudaStream_t st);
 cudaError_t debug_warp_hood(const float *pts, int m, int *out, int *count, int fp64, cudaStream_t st);
+cudaError_t debug_bridge_cta(const float *P, int hp, const float *Q, int hq, int *out, int fp64, cudaStream_t st);
 cudaError_t hull_turn(const float *points, float *rot, long long n, int sms, cudaStream_t st);
 cudaError_t hull_stitch(const float *points, long long n, const int32_t *lidx, const int32_t *lcount, int32_t *out,
                         int32_t *count, int sms, cudaStream_t st);
@@ -646,6 +647,17 @@ wg_status wg_debug_bridge(const float *P, int32_t hp, const float *Q, int32_t hq
     return debug_bridge(P, hp, Q, hq, d_pq, pred_mode == WG_PRED_FP64, S(stream)) == cudaSuccess
                ? WG_OK
                : WG_ERR_CUDA;
+}
+
+wg_status wg_debug_bridge_cta(const float *P, int32_t hp, const float *Q, int32_t hq, int32_t *d_pq,
+                              int32_t pred_mode, wg_stream_t stream)
+{
+    if (!P || !Q || !d_pq || hp < 1 || hq < 1) return WG_ERR_INVALID_VALUE;
+    DevInfo *d = nullptr;
+    wg_status st = dev_info(&d);
+    if (st != WG_OK) return st;
+    return debug_bridge_cta(P, hp, Q, hq, d_pq, pred_mode == WG_PRED_FP64, S(stream)) == cudaSuccess ? WG_OK
+                                                                                                   : WG_ERR_CUDA;
 }
 
 wg_status wg_debug_warp_hood(const float *points, int32_t m, int32_t *d_out, int32_t *d_out_count,

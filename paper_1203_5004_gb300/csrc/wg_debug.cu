@@ -44,6 +44,18 @@ __global__ void dbg_bridge_kernel(const float2 *P, int hp, const float2 *Q, int 
 }
 
 template <int MODE>
+__global__ void dbg_bridge_cta_kernel(const float2 *P, int hp, const float2 *Q, int hq, int *out)
+{
+    __shared__ int sh[2 * 32 + 2];
+    PredCount pc;
+    const int2 pq = bridge_cta<MODE>(pc, PtrHood{P}, hp, PtrHood{Q}, hq, sh);
+    if (threadIdx.x == 0) {
+        out[0] = pq.x;
+        out[1] = pq.y;
+    }
+}
+
+template <int MODE>
 __global__ void dbg_warp_hood_kernel(const float2 *pts, int m, int *out, int *count)
 {
     PredCount pc;
@@ -67,6 +79,16 @@ cudaError_t debug_orient(const float *p, long long ntri, int8_t *signs, unsigned
         dbg_orient_kernel<kModeFp64Only><<<grid, 256, 0, st>>>(pp, ntri, signs, fb);
     else
         dbg_orient_kernel<0><<<grid, 256, 0, st>>>(pp, ntri, signs, fb);
+    return cudaGetLastError();
+}
+
+cudaError_t debug_bridge_cta(const float *P, int hp, const float *Q, int hq, int *out, int fp64, cudaStream_t st)
+{
+    const float2 *p = reinterpret_cast<const float2 *>(P), *q = reinterpret_cast<const float2 *>(Q);
+    if (fp64)
+        dbg_bridge_cta_kernel<kModeFp64Only><<<1, 256, 0, st>>>(p, hp, q, hq, out);
+    else
+        dbg_bridge_cta_kernel<0><<<1, 256, 0, st>>>(p, hp, q, hq, out);
     return cudaGetLastError();
 }
 

@@ -267,6 +267,94 @@ __device__ int2 bridge_small(PredCount &pc, const PA &P, int hp, const QA &Q, in
     return make_int2(p, __shfl_sync(kFull, lo, p));
 }
 
+// Tangent corner T(p) of hood Q seen from p by the whole warp: each round the
+// 32 lanes test gLOW at 32 evenly spaced corners of the current bracket and
+// a ballot keeps the interval before the first corner that is not LOW, so a
+// round divides the bracket by 32 (ceil(log32 hq) rounds instead of
+// ceil(log2 hq) dependent steps). Returns T(p) in every lane.
+template <int MODE, class QA>
+__device__ int tangent_warp(PredCount &pc, float2 p, const QA &Q, int hq)
+{
+    const int lane = lane_id();
+    int lo = 0, hi = hq - 1;  // T(p) in [lo, hi]; gLOW(p, hi) is false
+    while (lo < hi) {
+        const int step = (hi - lo + 31) >> 5;
+        const int j = lo + lane * step;
+        const bool valid = j < hi;
+        bool low = false;
+        if (valid) low = orient<MODE>(pc, p, Q.pt(j), Q.pt(j + 1)) >= 0;
+        const unsigned nl = __ballot_sync(kFull, valid && !low);
+        const unsigned vm = __ballot_sync(kFull, valid);
+        if (nl) {
+            const int f = __ffs(nl) - 1;
+            hi = lo + f * step;
+            lo = f > 0 ? lo + (f - 1) * step + 1 : lo;
+        } else {
+            lo = lo + (31 - __clz(vm)) * step + 1;
+        }
+    }
+    return lo;
+}
+
+// Bridge of hoods P and Q by a whole CTA (every thread calls it with the
+// same arguments; nw = blockDim.x / 32 warps, at most 32), for hoods of many
+// thousands of corners: the multi-level bracketing of the paper's closing
+// section, with sampling on both hoods. Each round samples nw corners of
+// P's bracket, one per warp; each warp finds its corner's tangent corner on
+// Q with the 32-way search (tangent_warp) and evaluates the f vote; the
+// first corner whose vote is not LOW narrows P's bracket to one sampling
+// interval. Rounds: ceil(log_nw hp), each of ceil(log32 hq) warp rounds.
+// sh: 2 nw + 2 ints of shared memory. Returns (p, q) in every thread.
+template <int MODE, class PA, class QA>
+__device__ int2 bridge_cta(PredCount &pc, const PA &P, int hp, const QA &Q, int hq, int *sh)
+{
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int *vote = sh, *tang = sh + nw, *ctl = sh + 2 * nw;
+    int lo = 0, hi = hp - 1, thi = -1;  // p* in [lo, hi]; fLOW(hi) is false
+    while (lo < hi) {
+        const int step = (hi - lo + nw - 1) / nw;
+        const int i = lo + warp * step;
+        const bool valid = i < hi;
+        int t = 0;
+        bool low = false;
+        if (valid) {
+            const float2 pi = P.pt(i);
+            t = tangent_warp<MODE>(pc, pi, Q, hq);
+            low = orient<MODE>(pc, pi, Q.pt(t), P.pt(i + 1)) > 0;
+        }
+        if (lane == 0) {
+            vote[warp] = valid ? (low ? 1 : 0) : 2;
+            tang[warp] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int f = -1, last = -1;
+            for (int w = 0; w < nw; ++w) {
+                if (vote[w] == 2) break;
+                last = w;
+                if (vote[w] == 0) {
+                    f = w;
+                    break;
+                }
+            }
+            ctl[0] = f;
+            ctl[1] = last;
+        }
+        __syncthreads();
+        const int f = ctl[0], last = ctl[1];
+        if (f >= 0) {
+            thi = tang[f];
+            hi = lo + f * step;
+            lo = f > 0 ? lo + (f - 1) * step + 1 : lo;
+        } else {
+            lo = lo + last * step + 1;
+        }
+        __syncthreads();
+    }
+    const int q = thi >= 0 ? thi : tangent_warp<MODE>(pc, P.pt(lo), Q, hq);
+    return make_int2(lo, q);
+}
+
 // ---------------------------------------------------------------------------
 // Hood of up to 32 sorted, distinct points held one per lane (lanes [0, m)),
 // computed in registers by the paper's stages d = 1, 2, 4, 8, 16: at stage d

@@ -12,7 +12,9 @@
 // paper's classifications (binary search on the f votes of P, each with a
 // binary search of the g votes on Q); pairs whose hoods hold more than 64
 // corners together are handed to the whole warp (bridge_warp, the sampled
-// 32-way form of mam 1-5) and copied by the warp.
+// 32-way form of mam 1-5) and copied by the warp; pairs of more than 4096
+// corners (the late stages of dense hoods) are bridged by the whole block
+// with the multi-level search (bridge_cta).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -23,6 +25,7 @@ namespace wg {
 
 constexpr int kPlainThreads = 256;
 constexpr int kSmallPair = 64;
+constexpr int kHugePair = 4096;  // larger pairs: the whole block bridges them
 constexpr unsigned long long kLbFlagA = 1ull << 62, kLbFlagP = 2ull << 62;
 constexpr unsigned long long kLbMask = (1ull << 62) - 1;
 
@@ -66,6 +69,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_stage_kernel(PlainArgs a)
     __shared__ int s_bid;
     __shared__ int s_wsum[kPlainThreads / 32];
     __shared__ long long s_prefix;
+    __shared__ int s_nhuge, s_huge[kPlainThreads], s_pair[4], s_cta[2 * (kPlainThreads / 32) + 2];
     PredCount pc;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bid = (int)atomicAdd(a.ticket, 1u);
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_stage_kernel(PlainArgs a)
     }
     // Bridge of small pairs by the thread itself.
     int bp = -1, bq = 0, len = 0;
-    bool large = false;
+    bool large = false, huge = false;
     if (valid) {
         if (hp == 0 || hq == 0) {
             len = hp + hq;
@@ -114,9 +118,35 @@ __global__ void __launch_bounds__(kPlainThreads) plain_stage_kernel(PlainArgs a)
             bp = r.x;
             bq = r.y;
             len = bp + 1 + hq - bq;
-        } else {
+        } else if (hp + hq <= kHugePair) {
             large = true;
+        } else {
+            huge = true;
         }
+    }
+    // Huge pairs (the late stages): the whole block finds each bridge with
+    // the multi-level search, one pair after the other.
+    if (tid == 0) s_nhuge = 0;
+    __syncthreads();
+    if (huge) s_huge[atomicAdd(&s_nhuge, 1)] = tid;
+    __syncthreads();
+    for (int k = 0; k < s_nhuge; ++k) {
+        const int owner = s_huge[k];
+        if (tid == owner) {
+            s_pair[0] = pa;
+            s_pair[1] = hp;
+            s_pair[2] = qa;
+            s_pair[3] = hq;
+        }
+        __syncthreads();
+        const int2 r = bridge_cta<MODE>(pc, PtrHood{ixy + s_pair[0]}, s_pair[1], PtrHood{ixy + s_pair[2]},
+                                        s_pair[3], s_cta);
+        if (tid == owner) {
+            bp = r.x;
+            bq = r.y;
+            len = bp + 1 + hq - bq;
+        }
+        __syncthreads();
     }
     // Large pairs: the warp finds each bridge together.
     unsigned lm = __ballot_sync(kFull, large);
@@ -132,6 +162,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_stage_kernel(PlainArgs a)
             len = bp + 1 + hq - bq;
         }
     }
+    large = large || huge;  // both are copied by the warp
 
     // Block exclusive scan of merged lengths, then decoupled look-back.
     const int incl = warp_incl_sum(len);

@@ -211,6 +211,14 @@ def debug_bridge(P: torch.Tensor, Q: torch.Tensor, pred_mode: int = _lib.WG_PRED
     return r[0], r[1]
 
 
+def debug_bridge_cta(P: torch.Tensor, Q: torch.Tensor, pred_mode: int = _lib.WG_PRED_FILTERED, stream=None):
+    out = torch.empty(2, dtype=torch.int32, device=P.device)
+    check(load().wg_debug_bridge_cta(_ptr(_as_points(P)), P.shape[0], _ptr(_as_points(Q)), Q.shape[0], _ptr(out),
+                                     pred_mode, _stream(stream)), "wg_debug_bridge_cta")
+    r = out.cpu().tolist()
+    return r[0], r[1]
+
+
 def debug_warp_hood(points: torch.Tensor, pred_mode: int = _lib.WG_PRED_FILTERED, stream=None):
     m = points.shape[0]
     out = torch.empty(32, dtype=torch.int32, device=points.device)

@@ -561,3 +561,84 @@ def test_convex_hull_configs(wg, name, make):
     ps = make()
     got = wg.convex_hull(gpu_points(ps)).cpu().numpy()
     assert_same(got, oracle.convex_hull(ps.kx, ps.ky), f"hull {name}")
+
+
+# ---------------------------------------------------------------- shards (the multi-GPU exchange)
+@pytest.mark.parametrize("kind", ["uniform", "band", "arc", "duplicates", "columns", "gauss_x"])
+@pytest.mark.parametrize("k", [2, 3, 8])
+def test_virtual_shards_then_merge(wg, kind, k):
+    # The exchange a sharded run would make, on one GPU: k contiguous shards
+    # of one set are hulled by separate wg_upper_hood calls (as k ranks
+    # would), their corners (coordinates and global indices) are gathered in
+    # shard order, and one more call hulls the gathered corners. The hood of
+    # a union is the hood of the union of the shards' hoods, and repeats that
+    # straddle a shard boundary keep their first occurrence.
+    n = 1_000_003
+    ps = inputs.make(kind, n, 70 + k)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(n))
+    gathered = []
+    for r in range(k):
+        lo, hi = r * n // k, (r + 1) * n // k
+        h = wg.upper_hood(pts[lo:hi], workspace=ws)
+        gathered.append(h.to(torch.int64) + lo)
+    cand = torch.cat(gathered)
+    merged = wg.upper_hood(pts[cand].contiguous(), workspace=ws)
+    got = cand[merged.to(torch.int64)].cpu().numpy()
+    assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"{k} shards of {kind}")
+    assert wg.device_status(ws) == 0
+
+
+# ---------------------------------------------------------------- huge hoods (multi-level bridge)
+def _convex_chain(L):
+    # a strictly convex lattice chain: every primitive step (a, b) with
+    # a >= 1, |b| <= a and a + |b| <= L, by decreasing slope b / a
+    from math import gcd
+    steps = [(a, b) for a in range(1, L + 1) for b in range(-a, a + 1) if a + abs(b) <= L and gcd(a, abs(b)) == 1]
+    steps.sort(key=lambda v: -v[1] / v[0])
+    kx = np.concatenate([[0], np.cumsum([v[0] for v in steps])]).astype(np.int64)
+    ky = np.concatenate([[0], np.cumsum([v[1] for v in steps])]).astype(np.int64)
+    return kx, ky - ky.min()
+
+
+@pytest.mark.parametrize("L", [60, 120, 330])
+def test_bridge_cta_huge_hoods(wg, L):
+    # two convex chains of 10^3..3 10^4 corners, the second shifted right and
+    # by a random height, so that the bridge falls anywhere along both; the
+    # CTA search (multi-level bracketing) and the warp search must both give
+    # the oracle's bridge
+    kx, ky = _convex_chain(L)
+    m = kx.shape[0]
+    assert kx[-1] < inputs.G // 2 and ky.max() < inputs.G // 4
+    r = np.random.default_rng(L)
+    for trial in range(6):
+        a = int(r.integers(m // 4, m))
+        b = int(r.integers(m // 4, m))
+        dx = int(kx[a - 1]) + int(r.integers(1, 1000))
+        dy = int(r.integers(-int(ky.max()) // 2, int(ky.max()) // 2))
+        px, py = kx[:a], ky[:a] + inputs.G // 4
+        qx, qy = kx[:b] + dx, ky[:b] + inputs.G // 4 + dy
+        ref = oracle.bridge(px, py, qx, qy)
+        P = torch.from_numpy(inputs.to_float_points(px, py)).to(DEV)
+        Q = torch.from_numpy(inputs.to_float_points(qx, qy)).to(DEV)
+        assert wg.debug_bridge_cta(P, Q) == ref, (L, trial, a, b)
+        assert wg.debug_bridge_cta(P, Q, pred_mode=1) == ref
+        if a < 5000:
+            assert wg.debug_bridge(P, Q) == ref
+
+
+def test_bridge_cta_against_oracle_random(wg):
+    # the CTA search on the same hood pairs as the warp search tests
+    for kind in ("fine", "coarse", "arc", "concave"):
+        r = np.random.default_rng({"fine": 2, "coarse": 3, "arc": 13, "concave": 14}[kind] + 100)
+        for trial in range(150):
+            n = int(r.integers(2, {"arc": 400, "concave": 600}.get(kind, 3000)))
+            span = int(r.integers(2, 64)) if kind == "coarse" else inputs.G
+            pair = _hood_pair(r, n, span, kind)
+            if pair is None:
+                continue
+            kx, ky, hp, hq = pair
+            ref = oracle.bridge(kx[hp], ky[hp], kx[hq], ky[hq])
+            P = torch.from_numpy(inputs.to_float_points(kx[hp], ky[hp])).to(DEV)
+            Q = torch.from_numpy(inputs.to_float_points(kx[hq], ky[hq])).to(DEV)
+            assert wg.debug_bridge_cta(P, Q) == ref, (kind, trial)
