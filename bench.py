@@ -332,7 +332,7 @@ def run_batched(args, world, rank, local):
     ws = wagener.new_workspace(wagener.batched_workspace_size(offs), dev)
     stream = torch.cuda.current_stream(dev)
     if args.tile_config:
-        bopts = wagener.default_options(tile_config=args.tile_config)
+        bopts = wagener.default_options(tile_config=args.tile_config, batch_seg_tiles=args.batch_seg_tiles)
     elif args.no_autotune:
         bopts = None
     else:
@@ -658,6 +658,8 @@ def main():
     ap.add_argument("--compare", default="",
                     help="comma list of extra forms to time: counters, fp64_only, plain")
     ap.add_argument("--sets", type=int, default=100000, help="sets of the batched workload")
+    ap.add_argument("--batch-seg-tiles", type=int, default=0,
+                    help="batched, with --tile-config: tiles per segment of a large set (0: library choice)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
