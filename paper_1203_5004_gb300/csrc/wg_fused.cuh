@@ -578,6 +578,40 @@ struct Warp {
         return out;
     }
 
+    // The rules of point_rules for a strip of a tile that lies in one column
+    // (every x equal), over the whole strip in one unrolled pass on the y's:
+    // a repeat of the previous point goes, and so does a point with a higher
+    // point next (in the tile) when its previous point is in the column too or
+    // the column is not the set's first. The height rule is not applied: in
+    // the set's first column every point is a new height maximum, and the
+    // column rule leaves about one point per tile.
+    __device__ __forceinline__ unsigned column_rules(const float2 *tb, int sbase, int nvalid, float2 prev_pt,
+                                                     bool has_prev) const
+    {
+        constexpr int K = C::kK;
+        const float x = tb[sbase].x;
+        const float2 p0 = sbase > 0 ? tb[sbase - 1] : prev_pt;
+        bool same_col = (sbase > 0 || has_prev) && p0.x == x;
+        float yp = p0.y;
+        float yc = tb[sbase].y;
+        const bool later_col = x > xfirst;
+        unsigned out = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (j < nvalid) {
+                const bool hn = j + 1 < nvalid;
+                const float yn = hn ? tb[sbase + j + 1].y : yc;
+                const bool repeat = same_col && yp == yc;
+                const bool up = hn && yn > yc;
+                if (!(repeat || (up && (same_col || later_col)))) out |= 1u << j;
+                same_col = true;
+                yp = yc;
+                yc = yn;
+            }
+        }
+        return out;
+    }
+
     __device__ __forceinline__ void validate_strip(const float2 *tb, int sbase, int nvalid, float2 prev_pt,
                                                 bool has_prev) const
     {
@@ -656,7 +690,10 @@ struct Warp {
         const bool dead = !(ymax_mine > pm0) && ymax_mine < sm0;
         const unsigned live = __ballot_sync(kFull, !dead && nvalid > 0);
         unsigned surv = 0;
-        if (live) {
+        if (live && __popc(live) > 1 && tb[0].x == tb[cnt - 1].x) {
+            // The tile lies in one column.
+            if (!dead && nvalid > 0) surv = column_rules(tb, sbase, nvalid, prev_pt, has_prev);
+        } else if (live) {
             bool sheared = false;
             if (sh_skip > 0 && __popc(live) <= kShearBackoffLanes) {
                 --sh_skip;

@@ -204,6 +204,40 @@ def test_segments_per_cta(wg, spc):
         assert_same(got.cpu().numpy(), ref, f"cfg{cfg} spc{spc}")
 
 
+def _tall_columns(seed, first, mid, last, rest, rep_every):
+    """Sorted points with three tall columns: the set's first column (every
+    point a new height maximum), one in the middle and the last one; every
+    rep_every-th point of each column repeated, so that repeats fall on tile
+    edges somewhere; `rest` uniform points between them."""
+    r = np.random.default_rng(seed)
+    G = inputs.G
+    cols = []
+    for x, m in ((0, first), (G // 2 + 17, mid), (G - 1, last)):
+        ys = np.sort(r.choice(G, size=m, replace=False)).astype(np.int64)
+        ys = np.concatenate([ys, ys[::rep_every]])
+        cols.append((np.full(ys.shape, x, np.int64), ys))
+    kx = np.concatenate([c[0] for c in cols] + [r.integers(1, G - 1, size=rest)])
+    ky = np.concatenate([c[1] for c in cols] + [r.integers(0, G, size=rest)])
+    return inputs.PointSet(*inputs.sort_lex(kx, ky), name="tall_columns")
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3, 4])
+def test_tall_columns(wg, cfg):
+    # Tiles that lie in one column take their own path (the column rule over
+    # the strip, no height rule): the first column, where the height rule
+    # drops nothing, a middle column and the last one, with repeats.
+    T = TILE_POINTS[cfg]
+    opts = wg.default_options(tile_config=cfg)
+    for seed, (first, mid, last, rest, rep) in enumerate([
+            (7 * T + 3, 3 * T + 1, 2 * T - 1, 20000, 31),
+            (T - 1, T + 1, T, 5000, 7),
+            (40 * T + 11, 0 + 1, 9 * T, 300000, 97),
+            (3 * T, 5 * T, 3 * T, 0, 2)]):
+        ps = _tall_columns(seed, first, mid, last, rest, rep)
+        got = wg.upper_hood(gpu_points(ps), opts=opts).cpu().numpy()
+        assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"cfg{cfg} tall columns seed {seed}")
+
+
 def test_closed_form_all_corners(wg):
     ps = inputs.closed_form()
     got = wg.upper_hood(gpu_points(ps)).cpu().numpy()
