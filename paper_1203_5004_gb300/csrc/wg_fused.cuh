@@ -1217,20 +1217,22 @@ struct Warp {
 
     // Block-wide exclusive prefix sums over entries 0..n-1 (n <=
     // kMaxSegSingle) in order: thread t holds the contiguous entries
-    // [t M, t M + M) in registers. f(i) is entry i's value; g(i, before)
-    // receives its exclusive prefix. Returns the total. Every thread of the
-    // CTA calls it.
+    // [t m, t m + m) in registers, m = ceil(n / threads) (so that a short
+    // list is spread over the threads too). f(i) is entry i's value;
+    // g(i, before) receives its exclusive prefix. Returns the total. Every
+    // thread of the CTA calls it.
     template <class F, class G>
     __device__ int cta_scan(int n, int t, int gw, int *xsum, F f, G g) const
     {
         constexpr int nw = C::kW, nthreads = nw * 32;
         constexpr int M = (kMaxSegSingle + nthreads - 1) / nthreads;
-        const int c0 = t * M;
+        const int m = (n + nthreads - 1) / nthreads;
+        const int c0 = t * m;
         int v[M];
         int sum = 0;
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            v[j] = c0 + j < n ? f(c0 + j) : 0;
+            v[j] = j < m && c0 + j < n ? f(c0 + j) : 0;
             sum += v[j];
         }
         const int incl = warp_incl_sum(sum);
@@ -1245,7 +1247,7 @@ struct Warp {
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            if (c0 + j < n) g(c0 + j, before);
+            if (j < m && c0 + j < n) g(c0 + j, before);
             before += v[j];
         }
         return total;
@@ -1288,7 +1290,7 @@ struct Warp {
         constexpr size_t kScratch = kCtaBytes - nw * kStg;
         float2 *stg = reinterpret_cast<float2 *>(cta_base + kCtaBytes - (size_t)(gw + 1) * kStg);
         // control words and cross-warp slots at the start of shared memory
-        int *ctl = reinterpret_cast<int *>(cta_base);  // [0] smem hoods, [1] pairs ok
+        int *ctl = reinterpret_cast<int *>(cta_base);  // [0] smem hoods, [1] pairs ok, [2] copied here
         float *xpre = reinterpret_cast<float *>(ctl + 8);
         float *xsuf = xpre + 32;
         int *xsum = reinterpret_cast<int *>(xsuf + 32);
@@ -1386,7 +1388,8 @@ struct Warp {
                 long long htot = 0;
                 for (int w = 0; w < nw; ++w) htot += xsum[w];
                 ctl[0] = htot <= store_cap;
-                (void)any_unstaged;
+                // the result (at most htot corners) will be copied here
+                ctl[2] = ctl[0] && !any_unstaged && htot <= 8 * nthreads;
             }
             __syncthreads();
         }
@@ -1433,9 +1436,17 @@ struct Warp {
             if (t == 0) {
                 hdr->nlist = 0;  // nothing for the other warps to bridge
                 hdr->pair_done = 0;
+                if (ctl[2]) {
+                    // nor to copy: they may leave now
+                    hdr->nplan = 0;
+                    *args.arrivals = 0;
+                }
             }
             __syncthreads();
-            if (t == 0) release_tag(&hdr->phase1);
+            if (t == 0) {
+                release_tag(&hdr->phase1);
+                if (ctl[2]) release_tag(&hdr->phase2);
+            }
         } else {
             // 2 (with the grid). Publish the list; every warp bridges its
             // share of the pairs.
@@ -1618,8 +1629,9 @@ struct Warp {
                 }
             }
         }
+        if (t == 0) args.out_count[0] = total_out;
+        if (ctl[2]) return;  // phase 2 is out already
         if (t == 0) {
-            args.out_count[0] = total_out;
             hdr->nplan = here ? 0u : (unsigned)nl;
             *args.arrivals = 0;
         }
