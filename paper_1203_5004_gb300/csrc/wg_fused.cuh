@@ -55,6 +55,7 @@ __device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); 
 
 constexpr int kShearLanes = 3;         // more surviving strips than this: shear the tile
 constexpr int kShearBackoffLanes = 8;  // after failed trials, skip trials only up to this many
+constexpr int kPruneRounds = 16;       // neighbour-pruning rounds of a pending flush before the chain
 
 // The frame in which a tile's points are compared by height: y itself, or
 // the sheared y' = (y - y0) - s (x - x0). Shearing keeps every orientation.
@@ -437,86 +438,84 @@ struct Warp {
     // deletions may all be made at once. When a round deletes nothing, every
     // live entry is a strict right turn between its neighbours: the live
     // entries form a convex chain, the hood of the list (the paper's stages
-    // over these points, reached by local tests). The survivors are packed
-    // and the hood is merged into the running hood by one bridge (mam 1-5)
-    // and mam 6. If the rounds run out first, the survivors are pushed one by
-    // one by the monotone chain instead.
+    // over these points, reached by local tests), and it is merged into the
+    // running hood by one bridge (mam 1-5) and mam 6. The survivors are
+    // packed after every round, so that an entry's live neighbours are the
+    // adjacent entries (a shuffle each) and later rounds touch only the
+    // groups of 32 still occupied. If the rounds run out first, the
+    // survivors are pushed one by one by the monotone chain instead.
     __device__ __forceinline__ void flush_pending(RState &R)
     {
         constexpr int Q = C::kPCap / 32;
-        const int m = pn;
+        int m = pn;
         pn = 0;
         if (m == 0) return;
         float2 *L = pxy();
         int *Lid = pidx();
-        unsigned live[Q];
-        float2 mine[Q];
-        int mid[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const bool in = q * 32 + lane < m;
-            live[q] = __ballot_sync(kFull, in);
-            mine[q] = in ? L[q * 32 + lane] : make_float2(0.f, 0.f);
-            mid[q] = in ? Lid[q * 32 + lane] : 0;
-        }
         const int h0 = R.g + R.w;
         const bool anchor = h0 >= 1;
         const float2 Bv = anchor ? r_pt(R, h0 - 1) : make_float2(0.f, 0.f);
         bool convex = false;
-        for (int round = 0; round < 4; ++round) {
-            unsigned dead[Q];
+        for (int round = 0; round < kPruneRounds; ++round) {
+            // the live entries are L[0, m), packed: entry e's neighbours are
+            // e - 1 (the running hood's last corner for e = 0) and e + 1
+            const int nq = (m + 31) >> 5;
+            float2 mine[Q];
+            int mid[Q];
+            unsigned keep[Q];
             unsigned any = 0;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                dead[q] = 0;
-                if (live[q]) {
-                    bool d = false;
-                    if ((live[q] >> lane) & 1u) {
-                        // nearest live entries before and after entry 32 q + lane
-                        int pe = -1, ne = -1;
-                        const unsigned below = live[q] & ((1u << lane) - 1u);
-                        const unsigned above = lane < 31 ? live[q] & ~((2u << lane) - 1u) : 0u;
-                        if (below) pe = q * 32 + 31 - __clz(below);
+                keep[q] = 0;
+                if (q < nq) {
+                    const int e = q * 32 + lane;
+                    const bool in = e < m;
+                    mine[q] = in ? L[e] : make_float2(0.f, 0.f);
+                    mid[q] = in ? Lid[e] : 0;
+                }
+            }
 #pragma unroll
-                        for (int r = q - 1; r >= 0; --r)
-                            if (pe < 0 && live[r]) pe = r * 32 + 31 - __clz(live[r]);
-                        if (above) ne = q * 32 + __ffs(above) - 1;
-#pragma unroll
-                        for (int r = q + 1; r < Q; ++r)
-                            if (ne < 0 && live[r]) ne = r * 32 + __ffs(live[r]) - 1;
-                        if (ne >= 0 && (pe >= 0 || anchor)) {
-                            const float2 a = pe >= 0 ? L[pe] : Bv;
-                            d = orient<MODE>(pc, a, mine[q], L[ne]) >= 0;
-                        }
-                    }
-                    dead[q] = __ballot_sync(kFull, d);
-                    any |= dead[q];
+            for (int q = 0; q < Q; ++q) {
+                if (q < nq) {
+                    const int e = q * 32 + lane;
+                    const bool in = e < m;
+                    float2 a = shfl2(mine[q], (lane + 31) & 31);
+                    const float2 aw = q > 0 ? shfl2(mine[q > 0 ? q - 1 : 0], 31) : Bv;
+                    if (lane == 0) a = aw;
+                    float2 b = shfl2(mine[q], (lane + 1) & 31);
+                    const float2 bw = q + 1 < nq ? shfl2(mine[q + 1 < Q ? q + 1 : q], 0) : b;
+                    if (lane == 31) b = bw;
+                    const bool d = in && (e > 0 || anchor) && e + 1 < m && orient<MODE>(pc, a, mine[q], b) >= 0;
+                    const unsigned dead = __ballot_sync(kFull, d);
+                    any |= dead;
+                    keep[q] = __ballot_sync(kFull, in) & ~dead;
                 }
             }
             if (!any) {
                 convex = true;
                 break;
             }
+            // pack the survivors to the front of the list, in order
+            __syncwarp();
+            int base = 0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) live[q] &= ~dead[q];
-        }
-        // pack the live entries to the front of the list, in order
-        int base = 0;
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            if ((live[q] >> lane) & 1u) {
-                const int r = base + __popc(live[q] & ((1u << lane) - 1u));
-                L[r] = mine[q];
-                Lid[r] = mid[q];
+            for (int q = 0; q < Q; ++q) {
+                if (q < nq) {
+                    if ((keep[q] >> lane) & 1u) {
+                        const int r = base + __popc(keep[q] & ((1u << lane) - 1u));
+                        L[r] = mine[q];
+                        Lid[r] = mid[q];
+                    }
+                    base += __popc(keep[q]);
+                }
             }
-            base += __popc(live[q]);
+            __syncwarp();
+            m = base;
         }
-        __syncwarp();
-        if (convex && base > 1)
-            r_merge(R, L, Lid, base);
+        if (convex && m > 1)
+            r_merge(R, L, Lid, m);
         else
-            r_push(R, L, Lid, base);
+            r_push(R, L, Lid, m);
     }
 
     // Per-point elimination in one strip (not all dropped), by height: a
