@@ -620,7 +620,8 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "n": n, "seed": seed, "hull_corners": h,
                    "tile_config": int(opts.tile_config), "segments_per_cta": int(opts.segments_per_cta),
-                   "schedule": {1: "balanced", 2: "guided"}.get(int(opts.schedule), "library"),
+                   "schedule": {1: "balanced", 2: "guided", 3: "one CTA", 4: "small (one CTA, no tiles)"}.get(
+                       int(opts.schedule), "library"),
                    "l2": "input 8n bytes > 129 MB L2 (no flush)" if 8 * n > 129e6 else "input fits L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

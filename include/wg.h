@@ -85,7 +85,9 @@ typedef struct wg_options {
     int32_t schedule;        /* single set: 0 = library choice; 1 = balanced (one segment per warp,
                                 equal shares); 2 = guided (long segments first, then shorter ones
                                 claimed by warps as they become free); 3 = one CTA (balanced over
-                                the warps of a single CTA: for small inputs) */
+                                the warps of a single CTA); 4 = small (n <= WG_SMALL_MAX_N: one CTA
+                                holds the set in registers and prunes the survivors in shared
+                                memory, no tiles and no merge; the default up to that size) */
     int32_t batch_seg_tiles; /* batched: 0 = library choice (autotuned if wg_autotune_batched ran,
                                 else 128); else 8..4096 tiles per segment of a large set (larger
                                 sets are split over several warps) */
@@ -96,6 +98,8 @@ typedef struct wg_options {
 #define WG_SCHEDULE_BALANCED 1
 #define WG_SCHEDULE_GUIDED 2
 #define WG_SCHEDULE_ONE_CTA 3
+#define WG_SCHEDULE_SMALL 4
+#define WG_SMALL_MAX_N 8192
 
 /* Fills *opts with the defaults (filtered predicate, no counters, no
  * validation, library-chosen tiling). */

@@ -151,7 +151,7 @@ wg_status check_opts(const wg_options &o)
     if (o.pred_mode != WG_PRED_FILTERED && o.pred_mode != WG_PRED_FP64) return WG_ERR_INVALID_VALUE;
     if (o.tile_config < 0 || o.tile_config > kNumTileCfgs) return WG_ERR_INVALID_VALUE;
     if (o.segments_per_cta < 0 || o.segments_per_cta > 8) return WG_ERR_INVALID_VALUE;
-    if (o.schedule < 0 || o.schedule > WG_SCHEDULE_ONE_CTA) return WG_ERR_INVALID_VALUE;
+    if (o.schedule < 0 || o.schedule > WG_SCHEDULE_SMALL) return WG_ERR_INVALID_VALUE;
     if (o.batch_seg_tiles != 0 && (o.batch_seg_tiles < 8 || o.batch_seg_tiles > 4096)) return WG_ERR_INVALID_VALUE;
     return WG_OK;
 }
@@ -204,6 +204,7 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     int dev = 0;
     st = dev_info(&d, &dev);
     if (st != WG_OK) return st;
+    if (o.schedule == WG_SCHEDULE_SMALL && n > kSmallMaxN) return WG_ERR_INVALID_VALUE;
     if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), S(stream)) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 
     int cfg = o.tile_config, spc = o.segments_per_cta, sched = o.schedule;
@@ -212,7 +213,16 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
         if (cfg == 0) cfg = (t & 0xff) ? (t & 0xff) : kDefaultCfg;
         if (spc == 0) spc = ((t >> 8) & 0xff) ? ((t >> 8) & 0xff) : 1;
         if (sched == 0) sched = ((t >> 16) & 0xff) ? ((t >> 16) & 0xff)
-                                                    : (n <= kOneCtaMaxN ? WG_SCHEDULE_ONE_CTA : WG_SCHEDULE_BALANCED);
+                                : (n <= kSmallMaxN ? WG_SCHEDULE_SMALL
+                                                   : (n <= kOneCtaMaxN ? WG_SCHEDULE_ONE_CTA : WG_SCHEDULE_BALANCED));
+        // a tuned choice of the small path covers its bucket only up to the limit
+        if (sched == WG_SCHEDULE_SMALL && n > kSmallMaxN) sched = WG_SCHEDULE_BALANCED;
+    }
+    if (sched == WG_SCHEDULE_SMALL) {
+        return small_launch(points, n, out_idx, out_count, workspace, pred_mode_bits(o), o.validate ? 1 : 0,
+                            S(stream)) == cudaSuccess
+                   ? WG_OK
+                   : WG_ERR_CUDA;
     }
     // Segments are claimed dynamically by the warps of one resident wave of
     // CTAs; segments_per_cta scales the number of warps the schedule plans
@@ -528,10 +538,12 @@ wg_status wg_autotune(const float *points, int64_t n, int32_t *out_idx, int32_t 
     float best_ms = 1e30f;
     int best_cfg = kDefaultCfg, best_spc = 1, best_sched = WG_SCHEDULE_GUIDED;
     const int variants[][2] = {{WG_SCHEDULE_BALANCED, 1}, {WG_SCHEDULE_BALANCED, 2}, {WG_SCHEDULE_GUIDED, 1},
-                               {WG_SCHEDULE_ONE_CTA, 1}};
+                               {WG_SCHEDULE_ONE_CTA, 1}, {WG_SCHEDULE_SMALL, 1}};
     for (int cfg = 1; cfg <= kNumTileCfgs; ++cfg) {
         for (const auto &var : variants) {
             if (var[0] == WG_SCHEDULE_ONE_CTA && n > (int64_t(1) << 21)) continue;
+            // the small path has no tiles: timed once, with the first configuration
+            if (var[0] == WG_SCHEDULE_SMALL && (n > kSmallMaxN || cfg != 1)) continue;
             const int spc = var[1];
             o.tile_config = cfg;
             o.segments_per_cta = spc;

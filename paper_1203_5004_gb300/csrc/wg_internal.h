@@ -1,6 +1,8 @@
 // wg_internal.h -- structures shared by the host launch code and the kernels.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -81,6 +83,13 @@ constexpr int kStageCorners = 128;
 // Most segments of one single-set call (the final merge keeps per-segment
 // arrays of this size in one CTA's shared memory).
 constexpr int kMaxSegSingle = 4096;
+
+// Small sets (wg_small.cu): one CTA holds the whole set, up to this many points.
+constexpr long long kSmallMaxN = 8192;
+// Upper hood of points[0, n), 1 <= n <= kSmallMaxN, in one launch; hdr is the
+// workspace header (status and counters).
+cudaError_t small_launch(const float *points, long long n, int32_t *out_idx, int32_t *out_count, void *hdr,
+                         int mode, int validate, cudaStream_t stream);
 
 // Tile configurations (warps per CTA, points per lane (odd), tile buffers
 // per warp, running window). Index 1..kNumTileCfgs as exposed in the ABI.

@@ -238,6 +238,66 @@ def test_tall_columns(wg, cfg):
         assert_same(got, oracle.upper_hull(ps.kx, ps.ky), f"cfg{cfg} tall columns seed {seed}")
 
 
+SMALL_SIZES = (1, 2, 3, 15, 16, 17, 31, 33, 511, 512, 513, 4095, 4096, 4097, 8191, 8192)
+
+
+@pytest.mark.parametrize("kind", KINDS + ["gauss_disk"])
+def test_small_path(wg, kind):
+    # One CTA, 16 points per thread: sizes around the thread and warp edges
+    # up to the path's limit, both as the default and when forced.
+    ws = wg.new_workspace(wg.workspace_size(8192))
+    forced = wg.default_options(schedule=4)
+    for n in SMALL_SIZES:
+        ps = inputs.make(kind, n, n + 3)
+        ref = oracle.upper_hull(ps.kx, ps.ky)
+        assert_same(wg.upper_hood(gpu_points(ps), workspace=ws).cpu().numpy(), ref, f"{kind} n={n}")
+        assert_same(wg.upper_hood(gpu_points(ps), opts=forced, workspace=ws).cpu().numpy(), ref,
+                    f"{kind} n={n} forced")
+    assert wg.device_status(ws) == 0
+
+
+def test_small_path_modes_and_views(wg):
+    # float64-only predicate, counters, validation, an unaligned view and the
+    # closed form (every point a corner: the list stays whole)
+    ws = wg.new_workspace(wg.workspace_size(8192))
+    for kind in ("band", "arc", "duplicates"):
+        ps = inputs.make(kind, 8001, 11)
+        ref = oracle.upper_hull(ps.kx, ps.ky)
+        for o in (wg.default_options(pred_mode=1), wg.default_options(count_predicates=1),
+                  wg.default_options(validate=1)):
+            assert_same(wg.upper_hood(gpu_points(ps), opts=o, workspace=ws).cpu().numpy(), ref, f"{kind} modes")
+        base = torch.zeros((len(ps) + 1, 2), dtype=torch.float32, device=DEV)
+        base[1:] = gpu_points(ps)
+        assert base[1:].data_ptr() % 16 == 8
+        assert_same(wg.upper_hood(base[1:], workspace=ws).cpu().numpy(), ref, f"{kind} unaligned")
+    assert wg.device_status(ws) == 0
+    tests, _ = wg.read_counters(ws)
+    assert tests > 0
+    ps = inputs.closed_form()
+    got = wg.upper_hood(gpu_points(ps), opts=wg.default_options(schedule=4), workspace=ws).cpu().numpy()
+    assert_same(got, np.arange(4096, dtype=np.int32), "closed form, small path")
+
+
+def test_small_path_validation_and_limit(wg):
+    ps = inputs.uniform(8000, 5)
+    pts = gpu_points(ps)
+    ws = wg.new_workspace(wg.workspace_size(len(ps)))
+    o = wg.default_options(validate=1, schedule=4)
+    out = torch.empty(len(ps), dtype=torch.int32, device=DEV)
+    cnt = torch.empty(1, dtype=torch.int32, device=DEV)
+    bad = pts.clone()
+    bad[[4095, 4096]] = bad[[4096, 4095]]  # across a thread (and warp) edge
+    wg.upper_hood_into(bad, out, cnt, ws, o)
+    assert wg.device_status(ws) == 3
+    bad = pts.clone()
+    bad[5000, 1] = float(np.float32(0.3) + np.float32(2.0 ** -25))
+    wg.upper_hood_into(bad, out, cnt, ws, o)
+    assert wg.device_status(ws) == 4
+    big = inputs.uniform(8193, 1)
+    with pytest.raises(wg.WagenerError):
+        wg.upper_hood(gpu_points(big), opts=wg.default_options(schedule=4))
+
+
 def test_closed_form_all_corners(wg):
     ps = inputs.closed_form()
     got = wg.upper_hood(gpu_points(ps)).cpu().numpy()
