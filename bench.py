@@ -64,7 +64,8 @@ def _code_only(text: str) -> str:
 
 # The sources that define the fused kernel (device code and its instantiations).
 KERNEL_SOURCES = ("wg_device.cuh", "wg_fused.cuh", "wg_internal.h", "wg_fused.cu", "wg_fused_cfg1.cu",
-                  "wg_fused_cfg2.cu", "wg_fused_cfg3.cu", "wg_fused_cfg4.cu")
+                  "wg_fused_cfg2.cu", "wg_fused_cfg3.cu", "wg_fused_cfg4.cu", "wg_small.cu")
+SMALL_MAX_N = 8192  # the library's default path up to this size is the one-CTA small kernel
 
 
 def kernel_source_hash() -> str:
@@ -102,9 +103,9 @@ def profiled_traffic_per_point(workload: str):
     return float(m.group(1))
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, kernel: str = "fused"):
     """dram bytes per launch from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", f"fused_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -491,7 +492,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     if args.tile_config:
-        opts = wagener.default_options(tile_config=args.tile_config)
+        opts = wagener.default_options(tile_config=args.tile_config, schedule=args.schedule,
+                                       segments_per_cta=args.segments_per_cta)
     elif args.no_autotune:
         opts = wagener.default_options()
     else:
@@ -611,7 +613,9 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peak()
     alg_bytes = 8 * n + 4 * h + 4
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.workload)
+    small = int(opts.schedule) == 4 or (int(opts.schedule) == 0 and n <= SMALL_MAX_N)
+    kernel = "small_kernel" if small else "fused_kernel"
+    traffic = profiled_traffic(args.workload, "small" if small else "fused")
     cpu_gpts, reps, el, cores = time_oracle_strips(ps)
     cpu1_gpts, reps1, el1 = time_oracle(ps, budget_s=6.0, max_reps=10)
     line = {
@@ -626,7 +630,7 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "fused_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "kernel": kernel, "alg_bytes_per_launch": alg_bytes,
                      "launch_ms_median": launch_ms, "launches_timed": nl},
         "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 4 + 4 * hh},
@@ -659,6 +663,10 @@ def main():
     ap.add_argument("--compare", default="",
                     help="comma list of extra forms to time: counters, fp64_only, plain")
     ap.add_argument("--sets", type=int, default=100000, help="sets of the batched workload")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="single set, with --tile-config: 1 balanced, 2 guided, 3 one CTA, 4 small (0: library choice)")
+    ap.add_argument("--segments-per-cta", type=int, default=0,
+                    help="single set, with --tile-config: segments per resident warp (0: library choice)")
     ap.add_argument("--batch-seg-tiles", type=int, default=0,
                     help="batched, with --tile-config: tiles per segment of a large set (0: library choice)")
     args = ap.parse_args()
