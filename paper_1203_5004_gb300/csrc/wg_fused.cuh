@@ -5,40 +5,41 @@
 // copied to the host and back every stage. Here the whole schedule runs in one
 // persistent launch of warp streams:
 //
-//  * Every warp owns a segment: a contiguous range of one set. It streams the
-//    segment through its own shared-memory ring of S tiles (32 * K points
-//    each), filled by 1-D bulk copies (TMA) and tracked by its own mbarriers,
-//    so warps never wait for each other.
-//  * Per tile ("stages d = 1 .. 32K", fused):
-//      - exact elimination: a point p is dropped when some earlier point is at
-//        least as high and some later point (this tile, or the next tile,
-//        already resident) is strictly higher; p then lies on or below a
-//        segment between two input points and cannot be a corner. A lane whose
-//        whole strip of K points is dropped this way learns it from the strip
-//        maximum alone (no per-point pass). Where many strips survive (points
-//        along a sloped curve) the same test runs in the frame sheared by the
-//        tile's chord slope, with each height an interval that bounds its
-//        rounding. A repeat of the previous input point is dropped too (first
-//        occurrence wins), and so is a point with a strictly higher point
-//        directly above it and a point below it in its column or to its left;
-//      - a lane with survivors builds the hood of its strip serially (the
-//        paper's Section 3 strips);
-//      - surviving strip corners are appended, in order, to the warp's pending
-//        list, which collects several tiles.
-//  * A full pending list is merged by the paper's stages: d <= 16 in
-//    registers (warp_hood_regs), larger d over chunk hoods in shared memory
-//    with the bridge search (bridge_warp) and mam 6 compaction; the result is
-//    merged into the warp's running segment hood (a shared-memory window of
-//    its right end; older corners spill to the output array).
-//  * At the end of its segment a warp publishes the segment hood (indices in
-//    the output array; coordinates and indices staged in the workspace when
-//    they fit one window), its count and the segment's maximum y. The second
-//    of two neighbouring segments to be published bridges the pair. The CTA
-//    whose warp completes the last segment of a set (an atomic arrival count,
-//    no waiting) merges the segment hoods: a staircase of the segment maxima
-//    drops whole segments (the same exact rule), then the bridges of the
-//    remaining neighbours, dropping hoods that contribute nothing, and the
-//    kept ranges are copied to the output.
+//  * Every warp owns segments: contiguous ranges of one set, each a whole
+//    number of tiles (32 * K points). It streams them through its own
+//    shared-memory ring of S tiles, filled by 1-D bulk copies (TMA) and
+//    tracked by its own mbarriers, so warps never wait for each other.
+//  * Per tile, exact elimination: a point p goes when some earlier point is
+//    at least as high and some later point (this tile, or the next tile,
+//    already resident) is strictly higher; p then lies on or below a segment
+//    between two input points and cannot be a corner. A lane whose whole
+//    strip of K points goes learns it from the strip maximum alone. Where
+//    many strips survive (points along a sloped curve) the same test runs in
+//    the frame sheared by the tile's chord slope, each height an interval
+//    that bounds its rounding. A tile inside one column takes the column
+//    rule alone. Then the point rules: a repeat of the previous input point
+//    goes (first occurrence wins), and so does a point with a strictly
+//    higher point directly above it and a point below it in its column or
+//    to its left.
+//  * The survivors are appended, in input order, to the warp's pending list
+//    (several tiles' worth). A full list is flushed: rounds of neighbour
+//    pruning (each deletion rests on two input points) until the list is a
+//    convex chain, its hood, which one bridge (mam 1-5, probing the running
+//    hood's end first) and mam 6 merge into the warp's running segment hood
+//    (a shared-memory window of its right end; older corners spill to the
+//    output array).
+//  * Single set: at the end of a segment the warp publishes the segment hood
+//    (indices in the output array; coordinates and indices staged in the
+//    workspace when they fit one window), its count and the segment's
+//    maximum y. The CTA whose warp finishes last leads the final merge: a
+//    staircase of the segment maxima drops whole segments (the same exact
+//    rule); the bridges of adjacent listed hoods are found in its shared
+//    memory, or by every warp of the grid when the hoods do not fit; hoods
+//    that contribute nothing are dropped round by round; the kept ranges are
+//    copied to the output.
+//  * Batched: warps take items (sets, or segments of large sets) from a
+//    queue; the second publisher of two neighbouring segments bridges them,
+//    and the warp that publishes a set's last segment merges the set.
 #pragma once
 #include <cuda_runtime.h>
 
