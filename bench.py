@@ -265,6 +265,21 @@ def run_reference(args, world, rank):
         }
         print(json.dumps(line), flush=True)
         return
+    if args.workload == "sort26":
+        _, key = sort_input(0)
+        value, reps, el, _ = time_argsort(key, budget_s=30.0, max_reps=max(1, min(args.steps, 5)))
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
+            "steps": reps, "warmup": 0, "ms_per_step": el / reps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "device sort of 2^26 uniform grid points in random order (48-bit keys)",
+                       "n": SORT_N, "seed": SORT_SEED},
+            "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle (numpy stable argsort)",
+                             "sample": f"full input, {reps} runs"},
+            "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     kind, n, seed, desc = WORKLOADS[args.workload]
     ps = make_input(kind, n, seed)
     import oracle
@@ -287,6 +302,135 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+SORT_N, SORT_SEED = 1 << 26, 8
+
+
+def sort_input(rank: int):
+    """2^26 uniform grid points in a seeded random order (the sort workload)."""
+    from paper_1203_5004_gb300 import inputs
+    ps = inputs.uniform(SORT_N, rank_seed(SORT_SEED, rank))
+    order = np.random.default_rng(rank_seed(SORT_SEED + 1, rank)).permutation(SORT_N)
+    kx, ky = ps.kx[order], ps.ky[order]
+    pts = np.stack([kx, ky], axis=1).astype(np.float32) * np.float32(2.0 ** -24)
+    key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
+    return pts, key
+
+
+def time_argsort(key, budget_s=20.0, max_reps=5):
+    """The sort oracle (numpy's stable argsort of the 48-bit keys, one core)."""
+    reps, t0 = 0, time.perf_counter()
+    ref = None
+    while reps < max_reps and (reps == 0 or time.perf_counter() - t0 < budget_s):
+        ref = np.argsort(key, kind="stable")
+        reps += 1
+    el = time.perf_counter() - t0
+    return key.size * reps / el / 1e9, reps, el, ref
+
+
+def run_sort(args, world, rank, local):
+    """The device sort of unsorted points (the step before the path)."""
+    import ctypes
+    import torch
+    from paper_1203_5004_gb300 import _lib, wagener
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    n = SORT_N
+    h_pts, key = sort_input(rank)
+    pts = torch.from_numpy(h_pts).to(dev)
+    ws = wagener.new_workspace(wagener.sort_points_workspace_size(n), dev)
+    out = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = _lib.load()
+
+    def step():
+        _lib.check(lib.wg_sort_points(pts.data_ptr(), n, out.data_ptr(), perm.data_ptr(), ws.data_ptr(), ws.numel(),
+                                      stream.cuda_stream), "wg_sort_points")
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    K = max(1, min(args.steps, 50))
+    if args.profile:
+        for _ in range(K):
+            step()
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "workload": "sort uniform 2^26", "n": n, "steps": K}))
+        return
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(t0.elapsed_time(t1), pg, dev)
+    value = n * world * K / (total_ms * 1e-3) / 1e9
+    nl = 20
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    for i in range(nl):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    call_ms = float(np.median([a.elapsed_time(b) for a, b in zip(starts, ends)]))
+    # end to end: points from pinned host memory, the sort, the permutation back
+    hp = torch.from_numpy(h_pts).pin_memory()
+    hperm = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_steps = 5
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        pts.copy_(hp, non_blocking=True)
+        step()
+        hperm.copy_(perm, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_value = n * world * e2e_steps / (time.perf_counter() - te) / 1e9
+    if pg:
+        pg.barrier()
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    cpu, reps, el, ref = time_argsort(key)
+    same = bool(np.array_equal(hperm.numpy(), ref.astype(np.int32)))
+    peak, peak_kind = measured_peak()
+    alg_bytes = 8 * n + 12 * n  # points read once, sorted points and permutation written once
+    achieved = alg_bytes / (call_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "device sort of 2^26 uniform grid points in random order (48-bit keys)", "n": n,
+                   "seed": SORT_SEED, "passes": 6, "same_permutation_as_oracle": same,
+                   "l2": "input 8n bytes > 129 MB L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind, "kernel": "wg_sort_points (all launches of one call)",
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms_median": call_ms, "launches_timed": nl},
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": K * 32,
+        "clocks": clocks,
+        "cpu_baseline": {"value": cpu, "unit": "Gkeys/s", "cores": 1, "kind": "oracle (numpy stable argsort)",
+                         "sample": f"full input, {reps} runs, {el:.1f} s"},
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
 
 
 DEFAULT_COMPARE = {
@@ -655,7 +799,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS) + ["batched", "sort26"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-config", type=int, default=0, help="fixed tile configuration (0: autotune)")
     ap.add_argument("--profile", action="store_true",
@@ -673,6 +817,9 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "sort26":
+        run_sort(args, world, rank, local)
         return
     if args.workload == "batched":
         run_batched(args, world, rank, local)

@@ -162,6 +162,35 @@ wg_status wg_convex_hull(const float *points, int64_t n, int32_t *out_idx,
                          const wg_options *opts, wg_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Unsorted input. Section 2 takes its points sorted left to right; these
+ * calls supply that order on the device.
+ *
+ * wg_sort_points: sorts n grid points (each coordinate k * 2^-24 in [0, 1),
+ * any order) by (x, y): sorted_points[i] is the input point perm[i]. The sort
+ * is stable, so the copies of a repeated point keep their input order.
+ * points, sorted_points: device float[2n], 8-byte aligned, not overlapping;
+ * perm: device int32[n]; n <= 2^30 (WG_ERR_UNSUPPORTED beyond). The workspace
+ * (>= wg_sort_points_workspace_size(n) bytes, 256-byte aligned) needs no
+ * initialisation. A point off the grid is sorted by its coordinates rounded
+ * down to the grid.
+ *
+ * wg_upper_hood_unsorted: the upper hood of points given in any order: the
+ * sort, wg_upper_hood_ex on the sorted points, and the corners mapped back
+ * to input indices. A repeated point counts by its first copy in the input.
+ * The workspace (>= wg_upper_hood_unsorted_workspace_size(n) bytes) is
+ * zero-filled once, as for wg_upper_hood.
+ * ---------------------------------------------------------------------- */
+size_t wg_sort_points_workspace_size(int64_t n);
+wg_status wg_sort_points(const float *points, int64_t n, float *sorted_points,
+                         int32_t *perm, void *workspace, size_t ws_bytes,
+                         wg_stream_t stream);
+size_t wg_upper_hood_unsorted_workspace_size(int64_t n);
+wg_status wg_upper_hood_unsorted(const float *points, int64_t n,
+                                 int32_t *out_idx, int32_t *out_count,
+                                 void *workspace, size_t ws_bytes,
+                                 const wg_options *opts, wg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Many independent sets in one persistent launch. Set s is
  * points[offsets[s] .. offsets[s+1]) (each set sorted on its own); its
  * corners, as indices local to the set, go to out_idx[offsets[s] ...] and

@@ -50,6 +50,10 @@ SIGNATURES = {
     "wg_upper_hood_ex": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
     "wg_convex_hull_workspace_size": (_sz, [_i64]),
     "wg_convex_hull": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
+    "wg_sort_points_workspace_size": (_sz, [_i64]),
+    "wg_sort_points": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "wg_upper_hood_unsorted_workspace_size": (_sz, [_i64]),
+    "wg_upper_hood_unsorted": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
     "wg_upper_hood_plain_workspace_size": (_sz, [_i64]),
     "wg_upper_hood_plain": (_i32, [_vp, _i64, _vp, _vp, _vp, _sz, _OPT_P, _vp]),
     "wg_upper_hood_batched_workspace_size": (_sz, [_vp, _i32]),

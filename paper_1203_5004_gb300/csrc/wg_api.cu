@@ -322,6 +322,72 @@ wg_status wg_convex_hull(const float *points, int64_t n, int32_t *out_idx, int32
     return hull_stitch(points, n, lidx, lcnt, out_idx, out_count, d->sms, s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ unsorted input
+size_t wg_sort_points_workspace_size(int64_t n)
+{
+    if (n < 0) return 0;
+    return sort_workspace_bytes(n);
+}
+
+wg_status wg_sort_points(const float *points, int64_t n, float *sorted_points, int32_t *perm, void *workspace,
+                         size_t ws_bytes, wg_stream_t stream)
+{
+    if (n < 0 || n > kSortMaxN) return n < 0 ? WG_ERR_INVALID_VALUE : WG_ERR_UNSUPPORTED;
+    if (n == 0) return WG_OK;
+    if (!points || !sorted_points || !perm) return WG_ERR_INVALID_VALUE;
+    if ((reinterpret_cast<uintptr_t>(points) | reinterpret_cast<uintptr_t>(sorted_points)) & 7u)
+        return WG_ERR_INVALID_VALUE;
+    if (!workspace || ws_bytes < sort_workspace_bytes(n)) return WG_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return WG_ERR_INVALID_VALUE;
+    DevInfo *d = nullptr;
+    wg_status st = dev_info(&d);
+    if (st != WG_OK) return st;
+    return sort_launch(points, n, sorted_points, perm, workspace, S(stream)) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+}
+
+// Workspace: the single-set workspace | sorted points (8n) | permutation (4n)
+// | the sort's own workspace.
+static void unsorted_layout(int64_t n, size_t *off_pts, size_t *off_perm, size_t *off_sort, size_t *total)
+{
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    size_t o = align_up(kSingleWsBytes, 256);
+    *off_pts = o;
+    o = align_up(o + 8 * nn, 256);
+    *off_perm = o;
+    o = align_up(o + 4 * nn, 256);
+    *off_sort = o;
+    *total = o + sort_workspace_bytes(n);
+}
+
+size_t wg_upper_hood_unsorted_workspace_size(int64_t n)
+{
+    if (n < 0) return 0;
+    size_t a, b, c, t;
+    unsorted_layout(n, &a, &b, &c, &t);
+    return t;
+}
+
+wg_status wg_upper_hood_unsorted(const float *points, int64_t n, int32_t *out_idx, int32_t *out_count,
+                                 void *workspace, size_t ws_bytes, const wg_options *opts, wg_stream_t stream)
+{
+    if (n < 0 || n > kSortMaxN) return n < 0 ? WG_ERR_INVALID_VALUE : WG_ERR_UNSUPPORTED;
+    wg_status st =
+        check_common(points, n, out_idx, out_count, workspace, ws_bytes, wg_upper_hood_unsorted_workspace_size(n));
+    if (st != WG_OK) return st;
+    cudaStream_t s = S(stream);
+    if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+    size_t opts_off, operm, osort, total;
+    unsorted_layout(n, &opts_off, &operm, &osort, &total);
+    char *w = static_cast<char *>(workspace);
+    float *sorted = reinterpret_cast<float *>(w + opts_off);
+    int32_t *perm = reinterpret_cast<int32_t *>(w + operm);
+    if ((st = wg_sort_points(points, n, sorted, perm, w + osort, total - osort, stream)) != WG_OK) return st;
+    // corners of the sorted points, then mapped back to input indices
+    if ((st = wg_upper_hood_ex(sorted, n, out_idx, out_count, workspace, kSingleWsBytes, opts, stream)) != WG_OK)
+        return st;
+    return sort_map_launch(out_idx, out_count, perm, n, s) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
+}
+
 // ------------------------------------------------------------------ plain path
 // Workspace: header | two hood buffers (xy, idx) of n corners | two offset
 // arrays | look-back words of every stage | tickets of every stage.

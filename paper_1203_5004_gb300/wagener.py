@@ -100,6 +100,44 @@ def convex_hull(points: torch.Tensor, opts: Options | None = None, workspace: to
     return out[: int(cnt.item())]
 
 
+def sort_points_workspace_size(n: int) -> int:
+    return int(load().wg_sort_points_workspace_size(int(n)))
+
+
+def sort_points(points: torch.Tensor, workspace: torch.Tensor | None = None, stream=None):
+    """Grid points in any order sorted by (x, y) on the device, stably: returns
+    (sorted points float32 (n, 2), perm int32 (n,)) with sorted[i] = points[perm[i]]."""
+    points = _as_points(points)
+    n = points.shape[0]
+    dev = points.device
+    ws = workspace if workspace is not None else new_workspace(sort_points_workspace_size(n), dev)
+    out = torch.empty((max(n, 1), 2), dtype=torch.float32, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    check(load().wg_sort_points(_ptr(points), n, _ptr(out), _ptr(perm), _ptr(ws), ws.numel(), _stream(stream)),
+          "wg_sort_points")
+    return out[:n], perm[:n]
+
+
+def upper_hood_unsorted_workspace_size(n: int) -> int:
+    return int(load().wg_upper_hood_unsorted_workspace_size(int(n)))
+
+
+def upper_hood_unsorted(points: torch.Tensor, opts: Options | None = None, workspace: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """Indices (int32, on the device, into the input order) of the upper-hood
+    corners of grid points given in any order."""
+    points = _as_points(points)
+    n = points.shape[0]
+    dev = points.device
+    ws = workspace if workspace is not None else new_workspace(upper_hood_unsorted_workspace_size(n), dev)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    check(load().wg_upper_hood_unsorted(_ptr(points), n, _ptr(out), _ptr(cnt), _ptr(ws), ws.numel(),
+                                        ctypes.byref(opts) if opts else None, _stream(stream)),
+          "wg_upper_hood_unsorted")
+    return out[: int(cnt.item())]
+
+
 def upper_hood_plain(points: torch.Tensor, opts: Options | None = None, workspace: torch.Tensor | None = None,
                      stream=None) -> torch.Tensor:
     """Same result by the unfused schedule (one launch per stage)."""

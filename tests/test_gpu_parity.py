@@ -736,3 +736,50 @@ def test_bridge_cta_against_oracle_random(wg):
             P = torch.from_numpy(inputs.to_float_points(kx[hp], ky[hp])).to(DEV)
             Q = torch.from_numpy(inputs.to_float_points(kx[hq], ky[hq])).to(DEV)
             assert wg.debug_bridge_cta(P, Q) == ref, (kind, trial)
+
+
+# ---------------------------------------------------------------- unsorted input (device sort)
+def _shuffled(ps, seed):
+    r = np.random.default_rng(seed)
+    order = r.permutation(len(ps.kx))
+    return ps.kx[order], ps.ky[order]
+
+
+def _grid_points(kx, ky):
+    return torch.from_numpy(np.stack([kx, ky], axis=1).astype(np.float32) * np.float32(2.0 ** -24)).to(DEV)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "duplicates", "columns", "gauss_x", "band"])
+def test_sort_points(wg, kind):
+    # The permutation of a stable sort by (x, y) is unique: compared whole
+    # with numpy's stable argsort of the same 48-bit keys.
+    for n in (1, 2, 31, 4095, 4096, 4097, 100_003, 1_000_000):
+        kx, ky = _shuffled(inputs.make(kind, n, n + 1), n)
+        key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
+        ref = np.argsort(key, kind="stable").astype(np.int32)
+        sp, perm = wg.sort_points(_grid_points(kx, ky))
+        assert np.array_equal(perm.cpu().numpy(), ref), f"{kind} n={n}"
+        want = np.stack([kx[ref], ky[ref]], axis=1).astype(np.float32) * np.float32(2.0 ** -24)
+        assert np.array_equal(sp.cpu().numpy(), want), f"{kind} n={n} points"
+
+
+@pytest.mark.parametrize("kind", ["uniform", "arc", "duplicates", "columns", "gauss_x", "band"])
+def test_upper_hood_unsorted(wg, kind):
+    # corners of shuffled input, as input indices: the oracle on the stably
+    # sorted points, mapped back through the sort's permutation (a repeated
+    # point counts by its first copy in the input)
+    for n in (1, 5, 300, 8192, 8193, 250_001):
+        kx, ky = _shuffled(inputs.make(kind, n, n + 2), n + 9)
+        key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
+        order = np.argsort(key, kind="stable")
+        ref = order[oracle.upper_hull(kx[order], ky[order])].astype(np.int32)
+        got = wg.upper_hood_unsorted(_grid_points(kx, ky)).cpu().numpy()
+        assert_same(got, ref, f"{kind} n={n}")
+
+
+def test_sort_points_large(wg):
+    kx, ky = _shuffled(inputs.uniform(1 << 24, 2), 3)
+    key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
+    ref = np.argsort(key, kind="stable").astype(np.int32)
+    _, perm = wg.sort_points(_grid_points(kx, ky))
+    assert np.array_equal(perm.cpu().numpy(), ref)
