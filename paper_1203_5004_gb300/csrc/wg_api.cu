@@ -200,11 +200,11 @@ wg_status wg_upper_hood_ex(const float *points, int64_t n, int32_t *out_idx, int
     if (st != WG_OK) return st;
     st = check_common(points, n, out_idx, out_count, workspace, ws_bytes, wg_upper_hood_workspace_size(n));
     if (st != WG_OK) return st;
+    if (o.schedule == WG_SCHEDULE_SMALL && n > kSmallMaxN) return WG_ERR_INVALID_VALUE;
     DevInfo *d = nullptr;
     int dev = 0;
     st = dev_info(&d, &dev);
     if (st != WG_OK) return st;
-    if (o.schedule == WG_SCHEDULE_SMALL && n > kSmallMaxN) return WG_ERR_INVALID_VALUE;
     if (n == 0) return cudaMemsetAsync(out_count, 0, sizeof(int32_t), S(stream)) == cudaSuccess ? WG_OK : WG_ERR_CUDA;
 
     int cfg = o.tile_config, spc = o.segments_per_cta, sched = o.schedule;

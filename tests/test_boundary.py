@@ -64,6 +64,10 @@ def test_workspace_queries(lib):
     off = np.array([0, 5, 5, 70000], dtype=np.int64)
     assert lib.wg_upper_hood_batched_workspace_size(off.ctypes.data, 3) >= 256
     assert lib.wg_upper_hood_batched_workspace_size(None, 0) >= 256
+    # the sort keeps two key copies (8 bytes each), an index copy and the histograms
+    assert lib.wg_sort_points_workspace_size(1 << 20) >= 20 * (1 << 20)
+    assert lib.wg_upper_hood_unsorted_workspace_size(1 << 20) >= \
+        lib.wg_upper_hood_workspace_size(1 << 20) + 12 * (1 << 20) + lib.wg_sort_points_workspace_size(1 << 20)
 
 
 def test_argument_errors_without_device(lib):
@@ -91,5 +95,23 @@ def test_argument_errors_without_device(lib):
     assert lib.wg_upper_hood_ex(addr, 10, addr, addr, addr, ws_bytes, ctypes.byref(o), None) == 1
     # batched
     assert lib.wg_upper_hood_batched(addr, addr, -1, addr, addr, addr, ws_bytes, None, None) == 1
+    # the small-set schedule beyond its size, an unknown schedule
+    o = _lib.default_options(schedule=4)
+    assert lib.wg_upper_hood_ex(addr, 8193, addr, addr, addr, ws_bytes, ctypes.byref(o), None) == 1
+    o = _lib.default_options(schedule=5)
+    assert lib.wg_upper_hood_ex(addr, 10, addr, addr, addr, ws_bytes, ctypes.byref(o), None) == 1
+    # sort and unsorted input
+    sws = lib.wg_sort_points_workspace_size(100)
+    assert lib.wg_sort_points(addr, -1, addr, addr, addr, sws, None) == 1
+    assert lib.wg_sort_points(addr, (1 << 30) + 1, addr, addr, addr, sws, None) == 7
+    assert lib.wg_sort_points(addr, 10, None, addr, addr, sws, None) == 1
+    assert lib.wg_sort_points(addr, 10, addr, None, addr, sws, None) == 1
+    assert lib.wg_sort_points(addr + 4, 10, addr, addr, addr, sws, None) == 1
+    assert lib.wg_sort_points(addr, 10, addr, addr, addr, 16, None) == 2
+    assert lib.wg_sort_points(addr, 10, addr, addr, addr + 8, sws, None) == 1
+    uws = lib.wg_upper_hood_unsorted_workspace_size(100)
+    assert lib.wg_upper_hood_unsorted(addr, -1, addr, addr, addr, uws, None, None) == 1
+    assert lib.wg_upper_hood_unsorted(addr, 10, addr, addr, addr, 16, None, None) == 2
+    assert lib.wg_upper_hood_unsorted(addr, (1 << 30) + 1, addr, addr, addr, uws, None, None) == 7
     assert lib.wg_debug_bridge(addr, 0, addr, 1, addr, 0, None) == 1
     assert lib.wg_debug_warp_hood(addr, 33, addr, addr, 0, None) == 1
