@@ -12,6 +12,7 @@
 
 #include "wg.h"
 #include "wg_internal.h"
+#include "wg_sort.h"
 
 namespace wg {
 cudaError_t fused_launch(int cfg, const FusedArgs &args, int grid, int mode, cudaStream_t stream);

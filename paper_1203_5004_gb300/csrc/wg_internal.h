@@ -84,14 +84,6 @@ constexpr int kStageCorners = 128;
 // arrays of this size in one CTA's shared memory).
 constexpr int kMaxSegSingle = 4096;
 
-// Device sort (wg_sort.cu) of up to kSortMaxN grid points by (x, y), stable:
-// sorted points and the permutation (perm[i] = input index of sorted point i).
-constexpr long long kSortMaxN = 1LL << 30;
-size_t sort_workspace_bytes(long long n);
-cudaError_t sort_launch(const float *points, long long n, float *sorted, int32_t *perm, void *ws, cudaStream_t s);
-// out[i] = perm[out[i]] for i < *count (corners of the sorted points mapped back).
-cudaError_t sort_map_launch(int32_t *out, const int32_t *count, const int32_t *perm, long long n, cudaStream_t s);
-
 // Small sets (wg_small.cu): one CTA holds the whole set, up to this many points.
 constexpr long long kSmallMaxN = 8192;
 // Upper hood of points[0, n), 1 <= n <= kSmallMaxN, in one launch; hdr is the

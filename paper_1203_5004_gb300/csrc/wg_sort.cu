@@ -23,6 +23,7 @@
 
 #include "wg.h"
 #include "wg_internal.h"
+#include "wg_sort.h"
 
 namespace wg {
 
