@@ -171,8 +171,9 @@ wg_status wg_convex_hull(const float *points, int64_t n, int32_t *out_idx,
  * points, sorted_points: device float[2n], 8-byte aligned, not overlapping;
  * perm: device int32[n]; n <= 2^30 (WG_ERR_UNSUPPORTED beyond). The workspace
  * (>= wg_sort_points_workspace_size(n) bytes, 256-byte aligned) needs no
- * initialisation. A point off the grid is sorted by its coordinates rounded
- * down to the grid.
+ * initialisation. A point inside [0, 1)^2 but off the grid is sorted by its
+ * coordinates rounded down to the grid; coordinates outside [0, 1) are not
+ * supported (their order is unspecified, nothing is written out of range).
  *
  * wg_upper_hood_unsorted: the upper hood of points given in any order: the
  * sort, wg_upper_hood_ex on the sorted points, and the corners mapped back
