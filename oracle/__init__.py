@@ -12,9 +12,12 @@ contiguous strips in parallel threads and once more over the strip hoods (the
 CPU baseline of the measurements). This module only compiles them with gcc,
 loads them with ctypes and marshals numpy arrays.
 
+``sort_points`` (the order of unsorted input) is one numpy call.
+
 Parity status: every function here is pinned by ``tests/test_oracle.py``
 (brute force, closed forms, Qhull in general position, invariants, Python
-big-integer orientation).
+big-integer orientation; Python's own stable sort of coordinate pairs for
+``sort_points``).
 """
 from __future__ import annotations
 
@@ -138,6 +141,17 @@ def upper_hull_strips(kx, ky, threads: int | None = None) -> np.ndarray:
     if h < 0:
         raise MemoryError("oracle_upper_hull_strips: out of memory or threads")
     return out[:h].copy()
+
+
+def sort_points(kx, ky) -> np.ndarray:
+    """The order of points given in any order, sorted by (x, y) and stable
+    (the step before the path: Section 2 takes its points sorted): perm with
+    (kx, ky)[perm] sorted lexicographically and equal points in input order.
+    One library step, numpy's stable sort of the 48-bit keys kx 2^24 + ky
+    (which order grid points exactly as (x, y))."""
+    kx = np.asarray(kx, dtype=np.int64)
+    ky = np.asarray(ky, dtype=np.int64)
+    return np.argsort((kx << 24) | ky, kind="stable").astype(np.int32)
 
 
 def upper_hull_brute(kx, ky) -> np.ndarray:

@@ -752,11 +752,10 @@ def _grid_points(kx, ky):
 @pytest.mark.parametrize("kind", ["uniform", "duplicates", "columns", "gauss_x", "band"])
 def test_sort_points(wg, kind):
     # The permutation of a stable sort by (x, y) is unique: compared whole
-    # with numpy's stable argsort of the same 48-bit keys.
+    # with the oracle's.
     for n in (1, 2, 31, 4095, 4096, 4097, 100_003, 1_000_000):
         kx, ky = _shuffled(inputs.make(kind, n, n + 1), n)
-        key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
-        ref = np.argsort(key, kind="stable").astype(np.int32)
+        ref = oracle.sort_points(kx, ky)
         sp, perm = wg.sort_points(_grid_points(kx, ky))
         assert np.array_equal(perm.cpu().numpy(), ref), f"{kind} n={n}"
         want = np.stack([kx[ref], ky[ref]], axis=1).astype(np.float32) * np.float32(2.0 ** -24)
@@ -770,8 +769,7 @@ def test_upper_hood_unsorted(wg, kind):
     # point counts by its first copy in the input)
     for n in (1, 5, 300, 8192, 8193, 250_001):
         kx, ky = _shuffled(inputs.make(kind, n, n + 2), n + 9)
-        key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
-        order = np.argsort(key, kind="stable")
+        order = oracle.sort_points(kx, ky)
         ref = order[oracle.upper_hull(kx[order], ky[order])].astype(np.int32)
         got = wg.upper_hood_unsorted(_grid_points(kx, ky)).cpu().numpy()
         assert_same(got, ref, f"{kind} n={n}")
@@ -779,7 +777,6 @@ def test_upper_hood_unsorted(wg, kind):
 
 def test_sort_points_large(wg):
     kx, ky = _shuffled(inputs.uniform(1 << 24, 2), 3)
-    key = (kx.astype(np.int64) << 24) | ky.astype(np.int64)
-    ref = np.argsort(key, kind="stable").astype(np.int32)
+    ref = oracle.sort_points(kx, ky)
     _, perm = wg.sort_points(_grid_points(kx, ky))
     assert np.array_equal(perm.cpu().numpy(), ref)

@@ -445,3 +445,43 @@ def test_convex_hull_degenerate():
     kx = [0, 0, 1, 2, 2, 2]
     ky = [0, 2, 1, 0, 1, 2]
     assert oracle.convex_hull(kx, ky).tolist() == [0, 1, 5, 3]
+
+
+# ---------------------------------------------------------------- sort (the step before the path)
+@pytest.mark.parametrize("n,seed", [(0, 0), (1, 1), (2, 2), (50, 3), (1000, 4), (5000, 5)])
+def test_sort_points_matches_python_sorted(n, seed):
+    # Python's sort is stable and compares the (x, y) pairs themselves: an
+    # independent statement of the same order
+    r = np.random.default_rng(seed)
+    kx = r.integers(0, 8, size=n)        # few distinct x: ties in x
+    ky = r.integers(0, 1 << 24, size=n)
+    ky[r.random(n) < 0.3] = 5            # repeated points
+    got = oracle.sort_points(kx, ky)
+    want = sorted(range(n), key=lambda i: (int(kx[i]), int(ky[i])))
+    assert got.tolist() == want
+
+
+def test_sort_points_invariants():
+    r = np.random.default_rng(9)
+    kx = r.integers(0, 1 << 24, size=20_000)
+    ky = r.integers(0, 1 << 24, size=20_000)
+    kx[::7] = kx[0]
+    ky[::11] = ky[3]
+    perm = oracle.sort_points(kx, ky)
+    assert sorted(perm.tolist()) == list(range(kx.size))              # a permutation
+    a, b = kx[perm], ky[perm]
+    assert np.all((a[1:] > a[:-1]) | ((a[1:] == a[:-1]) & (b[1:] >= b[:-1])))  # sorted by (x, y)
+    same = (a[1:] == a[:-1]) & (b[1:] == b[:-1])
+    assert np.all(perm[1:][same] > perm[:-1][same])                  # stable
+
+
+def test_sort_points_planted_unstable_sort_fails():
+    # an unstable sort of the same keys is a plausible slip; the pin above
+    # must tell it apart on repeated points
+    kx = np.array([3, 1, 3, 1, 3] * 40)
+    ky = np.array([2, 9, 2, 9, 2] * 40)
+    unstable = np.argsort((kx.astype(np.int64) << 24) | ky, kind="quicksort")[::-1]
+    unstable = unstable[np.argsort((kx[unstable].astype(np.int64) << 24) | ky[unstable], kind="stable")]
+    want = sorted(range(kx.size), key=lambda i: (int(kx[i]), int(ky[i])))
+    assert unstable.tolist() != want
+    assert oracle.sort_points(kx, ky).tolist() == want
