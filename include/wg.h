@@ -14,7 +14,8 @@
  * Input contract shared by every entry point
  *   - points: float32 pairs (x, y), interleaved, 8-byte aligned; x and y are
  *     integers times 2^-24 in [0, 1) (the "grid"); sorted lexicographically by
- *     (x, y). Grid coordinates make every coordinate difference exact in
+ *     (x, y), except for wg_sort_points and wg_upper_hood_unsorted, which take
+ *     them in any order. Grid coordinates make every coordinate difference exact in
  *     float32, which the orientation predicate relies on (see wg_options).
  *     Off-grid or unsorted input gives unspecified (but memory-safe) output
  *     unless validation is enabled.
@@ -22,8 +23,10 @@
  *     (order is lexicographic); a point equal to an earlier point is never a
  *     corner (first occurrence wins); collinear points are not corners (each
  *     corner is a strict right turn); any n >= 0 is accepted.
- *   - Output: the input indices of the corners, strictly increasing, and
- *     their count. n = 0 gives count 0; otherwise index 0 is always first.
+ *   - Output of the upper-hood calls: the input indices of the corners, left
+ *     to right (strictly increasing for sorted input), and their count. n = 0
+ *     gives count 0; otherwise the first point is always the first corner.
+ *     wg_convex_hull and wg_upper_hood_unsorted state their own order.
  *
  * Ownership and asynchrony
  *   - The caller owns every buffer. The library never allocates device memory
