@@ -280,6 +280,36 @@ def run_reference(args, world, rank):
         }
         print(json.dumps(line), flush=True)
         return
+    if args.workload in ("hull26", "bridge_cta"):
+        import oracle
+        reps = max(1, min(args.steps, 5))
+        if args.workload == "hull26":
+            kind, n, seed, desc = WORKLOADS["uniform26"]
+            ps = make_input(kind, n, seed)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                oracle.convex_hull(ps.kx, ps.ky)
+            el = time.perf_counter() - t0
+            value, unit, wl = n * reps / el / 1e9, "Gpoints/s", "convex hull of the " + desc
+        else:
+            from paper_1203_5004_gb300 import inputs
+            kx, ky = convex_chain(330)
+            px, py = kx, ky + inputs.G // 4
+            qx, qy = kx + int(kx[-1]) + 500, ky + inputs.G // 4 + int(ky.max()) // 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                oracle.bridge(px, py, qx, qy)
+            el = time.perf_counter() - t0
+            value, unit, wl = reps / el, "bridges/s", f"bridge of two convex chains of {kx.shape[0]} corners each"
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": reps,
+            "warmup": 0, "ms_per_step": el / reps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": {"workload": wl},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": f"{reps} runs"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     kind, n, seed, desc = WORKLOADS[args.workload]
     ps = make_input(kind, n, seed)
     import oracle
@@ -433,6 +463,193 @@ def run_sort(args, world, rank, local):
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def run_hull(args, world, rank, local):
+    """The full convex hull (the title problem) of the 2^26 uniform set."""
+    import torch
+    from paper_1203_5004_gb300 import _lib, wagener
+    import oracle
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    kind, n, seed, desc = WORKLOADS["uniform26"]
+    ps = make_input(kind, n, rank_seed(seed, rank))
+    h_pts = ps.points()
+    pts = torch.from_numpy(h_pts).to(dev)
+    ws = wagener.new_workspace(wagener.convex_hull_workspace_size(n), dev)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = _lib.load()
+
+    def step():
+        _lib.check(lib.wg_convex_hull(pts.data_ptr(), n, out.data_ptr(), cnt.data_ptr(), ws.data_ptr(), ws.numel(),
+                                      None, stream.cuda_stream), "wg_convex_hull")
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    h = int(cnt.item())
+    K = max(1, min(args.steps, 500))
+    if args.profile:
+        for _ in range(K):
+            step()
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "workload": "convex hull " + desc, "n": n, "steps": K}))
+        return
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(t0.elapsed_time(t1), pg, dev)
+    value = n * world * K / (total_ms * 1e-3) / 1e9
+    nl = 20
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    for i in range(nl):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    call_ms = float(np.median([a.elapsed_time(b) for a, b in zip(starts, ends)]))
+    hp = torch.from_numpy(h_pts).pin_memory()
+    hout = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_steps = 5
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        pts.copy_(hp, non_blocking=True)
+        step()
+        hh = int(cnt.item())
+        hout[:hh].copy_(out[:hh])
+    torch.cuda.synchronize(dev)
+    e2e_value = n * world * e2e_steps / (time.perf_counter() - te) / 1e9
+    if pg:
+        pg.barrier()
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    reps, tc = 0, time.perf_counter()
+    ref = None
+    while reps < 5 and (reps == 0 or time.perf_counter() - tc < 20.0):
+        ref = oracle.convex_hull(ps.kx, ps.ky)
+        reps += 1
+    el = time.perf_counter() - tc
+    same = bool(np.array_equal(hout[:h].numpy(), ref))
+    peak, peak_kind = measured_peak()
+    # two upper-hood passes over the points, the turned copy written once, the corners
+    alg_bytes = 8 * n + 8 * n + 8 * n + 4 * h + 4
+    achieved = alg_bytes / (call_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpoints/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "convex hull of the " + desc, "n": n, "seed": seed, "hull_corners": h,
+                   "same_corners_as_oracle": same, "l2": "input 8n bytes > 129 MB L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_kind, "kernel": "wg_convex_hull (all launches of one call)",
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms_median": call_ms, "launches_timed": nl},
+        "e2e": {"value": e2e_value, "unit": "Gpoints/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 + 4 * h},
+        "gpu_launches": K * 5,
+        "clocks": clocks,
+        "cpu_baseline": {"value": n * reps / el / 1e9, "unit": "Gpoints/s", "cores": 1,
+                         "kind": "oracle (upper and lower monotone chains)", "sample": f"full input, {reps} runs"},
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def convex_chain(L: int):
+    """A strictly convex lattice chain: every primitive step (a, b) with
+    a >= 1, |b| <= a and a + |b| <= L, by decreasing slope (a hood of many
+    thousands of corners for the bridge searches)."""
+    from math import gcd
+    steps = [(a, b) for a in range(1, L + 1) for b in range(-a, a + 1) if a + abs(b) <= L and gcd(a, abs(b)) == 1]
+    steps.sort(key=lambda v: -v[1] / v[0])
+    kx = np.concatenate([[0], np.cumsum([v[0] for v in steps])]).astype(np.int64)
+    ky = np.concatenate([[0], np.cumsum([v[1] for v in steps])]).astype(np.int64)
+    return kx, ky - ky.min()
+
+
+def run_bridge(args, world, rank, local):
+    """The bridge of two huge hoods (paper Section 2, mam 1-5): the CTA's
+    multi-level bracketing search against the one-warp search."""
+    import torch
+    from paper_1203_5004_gb300 import inputs, wagener
+    import oracle
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kx, ky = convex_chain(330)
+    m = int(kx.shape[0])
+    dx = int(kx[-1]) + 500
+    px, py = kx, ky + inputs.G // 4
+    qx, qy = kx + dx, ky + inputs.G // 4 + int(ky.max()) // 3
+    ref = oracle.bridge(px, py, qx, qy)
+    P = torch.from_numpy(inputs.to_float_points(px, py)).to(dev)
+    Q = torch.from_numpy(inputs.to_float_points(qx, qy)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    from paper_1203_5004_gb300 import _lib
+    lib = _lib.load()
+    pq = torch.empty(2, dtype=torch.int32, device=dev)
+    res = {}
+    K = max(1, min(args.steps, 200))
+    for name, fn, raw in (("cta", wagener.debug_bridge_cta, lib.wg_debug_bridge_cta),
+                          ("warp", wagener.debug_bridge, lib.wg_debug_bridge)):
+        res[name + "_same"] = bool(tuple(fn(P, Q)) == tuple(ref))
+
+        def call():
+            _lib.check(raw(P.data_ptr(), m, Q.data_ptr(), m, pq.data_ptr(), 0, stream.cuda_stream), name)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(K):
+            call()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name + "_us"] = a.elapsed_time(b) / K * 1e3
+    if rank != 0:
+        return
+    tc = time.perf_counter()
+    for _ in range(20):
+        oracle.bridge(px, py, qx, qy)
+    cpu_us = (time.perf_counter() - tc) / 20 * 1e6
+    line = {
+        "metric": METRIC, "value": 1e6 / res["cta_us"], "unit": "bridges/s", "n_gpus": 1, "steps": K,
+        "warmup": 1, "ms_per_step": res["cta_us"] / 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"bridge of two convex chains of {m} corners each (one launch per bridge, "
+                               "back to back on the device)",
+                   "corners_per_hood": m, "same_bridge_as_oracle": res["cta_same"] and res["warp_same"]},
+        "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                     "traffic": None, "kernel": "bridge_cta (one CTA)"},
+        "compare": {"warp_search_us": res["warp_us"], "cta_search_us": res["cta_us"]},
+        "e2e": {"value": None, "unit": "bridges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8},
+        "gpu_launches": K,
+        "cpu_baseline": {"value": 1e6 / cpu_us, "unit": "bridges/s", "cores": 1, "kind": "oracle (monotone chain "
+                         "over both hoods)", "sample": "20 runs"},
+    }
+    print(json.dumps(line), flush=True)
 
 
 DEFAULT_COMPARE = {
@@ -801,7 +1018,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform26", choices=sorted(WORKLOADS) + ["batched", "sort26"])
+    ap.add_argument("--workload", default="uniform26",
+                    choices=sorted(WORKLOADS) + ["batched", "sort26", "hull26", "bridge_cta"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-config", type=int, default=0, help="fixed tile configuration (0: autotune)")
     ap.add_argument("--profile", action="store_true",
@@ -822,6 +1040,12 @@ def main():
         return
     if args.workload == "sort26":
         run_sort(args, world, rank, local)
+        return
+    if args.workload == "hull26":
+        run_hull(args, world, rank, local)
+        return
+    if args.workload == "bridge_cta":
+        run_bridge(args, world, rank, local)
         return
     if args.workload == "batched":
         run_batched(args, world, rank, local)
